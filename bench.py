@@ -1,0 +1,362 @@
+#!/usr/bin/env python3
+"""Benchmark of the dual-select FMA FFT on one B300 (or N replicas).
+
+Workload (one "step"): forward FP16 dual-select FFTs with exact x0.5 per
+pass of one 1 GiB batch at each N in {2^10, 2^12, 2^14, 2^16}
+(batch = 2^30 / (4 N) signals; re/im i.i.d. uniform[-1, 1], seeded).
+``value`` = transforms/s over the whole step (all N, all ranks).
+
+Also reported on the same JSON line:
+  roofline     : the dominant kernel's algorithmic bytes (read + write of the
+                 batch) / its CUDA-event launch time, against the measured
+                 HBM copy bandwidth;
+  per_n        : transforms/s, GB/s, fraction of roofline, and relative L2
+                 error vs an FP64 FFT (numpy) on sampled signals, per N;
+  fp32_plain   : the FP32 form (no scaling) on the same bytes per N;
+  e2e          : the same metric with the input copied from pinned host
+                 memory and the output copied back inside the timed region;
+  cpu_baseline : the CPU oracle (op-by-op emulation) on a bounded sample;
+  clocks       : nvidia-smi samples taken during the timed region.
+
+``--impl reference`` times the CPU oracle itself on the same workload (a
+bounded sample per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "transforms/s & % HBM roofline, FP16 vs FP32 at stated FP64 error; serve p99 ms"
+LOG2NS = (10, 12, 14, 16)
+BATCH_BYTES = 1 << 30
+PRECISION = "fp16"
+FACTORIZATION = "dual_select"
+CPU_SAMPLE_DIV = 128         # oracle sample: batch / 128 signals per N
+
+
+def batch_for(log2n: int, precision: str = PRECISION) -> int:
+    eb = 8 if precision == "fp32" else 4
+    return BATCH_BYTES // (eb << log2n)
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons (200 ms)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max((float(r[3]) for r in rows if r[3].replace(".", "").isdigit()), default=None)}
+
+
+# ---------------------------------------------------------------------------
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def error_vs_fp64(plan, x_dev, y_dev, log2n, precision, scaled, samples=4):
+    """Relative L2 error of sampled outputs vs numpy's FP64 FFT of the same
+    (already rounded) inputs."""
+    from paper_2604_00567_b300 import signals
+    n = 1 << log2n
+    import torch
+    idx = torch.as_tensor(np.linspace(0, x_dev.shape[0] - 1, samples).astype(np.int64), device=x_dev.device)
+    xs = signals.from_torch(x_dev.index_select(0, idx), precision)
+    ys = signals.from_torch(y_dev.index_select(0, idx), precision)
+    ref = np.fft.fft(xs, axis=-1) / (n if scaled else 1)
+    return float(np.linalg.norm((ys - ref).ravel()) / np.linalg.norm(ref.ravel()))
+
+
+def run_ours(args):
+    import torch
+    import paper_2604_00567_b300 as dsfft
+    from paper_2604_00567_b300 import signals
+
+    world, rank, local = dist_setup()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    hbm_peak, peak_kind = measured_peaks()
+
+    log2ns = [l for l in args.log2n]
+    plans, xs, ys = {}, {}, {}
+    for l in log2ns:
+        plans[l] = dsfft.Plan(1 << l, PRECISION, FACTORIZATION)
+        xs[l] = signals.device_signal(batch_for(l), 1 << l, PRECISION, seed=1000 * rank + l, device=dev)
+        ys[l] = torch.empty_like(xs[l])
+    stream = torch.cuda.current_stream()
+
+    def step(events=None):
+        for i, l in enumerate(log2ns):
+            if events is not None:
+                events[i][0].record(stream)
+            plans[l].exec(xs[l], out=ys[l], stream=stream)
+            if events is not None:
+                events[i][1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    K = args.steps
+    evs = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in log2ns]
+           for _ in range(K)]
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for s in range(K):
+        step(evs[s])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop()
+    ms_total = allreduce_max(t_start.elapsed_time(t_end), world)
+    ms_per_step = ms_total / K
+    transforms_per_step = sum(batch_for(l) for l in log2ns)
+    value = world * transforms_per_step / (ms_per_step / 1e3)
+
+    per_n = {}
+    dominant = None
+    for i, l in enumerate(log2ns):
+        ms = statistics.mean(evs[s][i][0].elapsed_time(evs[s][i][1]) for s in range(K))
+        nbytes = 2 * batch_for(l) * (4 << l)
+        gbs = nbytes / (ms / 1e3) / 1e9
+        per_n[f"2^{l}"] = {
+            "batch": batch_for(l), "ms_per_launch": round(ms, 4),
+            "transforms_per_s": batch_for(l) / (ms / 1e3), "GB_per_s": round(gbs, 1),
+            "frac_of_hbm": round(gbs / hbm_peak, 4), "launches": plans[l].info()["launches"],
+            "rel_l2_vs_fp64": error_vs_fp64(plans[l], xs[l], ys[l], l, PRECISION, plans[l].scale_forward),
+        }
+        if dominant is None or ms > dominant[1]:
+            dominant = (l, ms, nbytes, gbs)
+    l, ms, nbytes, gbs = dominant
+    roofline = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(gbs / hbm_peak, 4), "traffic": None,
+                "kernel": f"fused_fft_kernel fp16 N=2^{l}", "peak_kind": peak_kind,
+                "algorithmic_bytes_per_launch": nbytes}
+
+    # FP32 plain form on the same bytes per N (separate timing, not in value)
+    fp32 = {}
+    for l in log2ns:
+        p32 = dsfft.Plan(1 << l, "fp32", FACTORIZATION)
+        x32 = signals.device_signal(batch_for(l, "fp32"), 1 << l, "fp32", seed=77 + l, device=dev)
+        y32 = torch.empty_like(x32)
+        for _ in range(3):
+            p32.exec(x32, out=y32)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(max(3, K)):
+            p32.exec(x32, out=y32)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / max(3, K)
+        nb = 2 * batch_for(l, "fp32") * (8 << l)
+        fp32[f"2^{l}"] = {"transforms_per_s": batch_for(l, "fp32") / (ms / 1e3),
+                          "GB_per_s": round(nb / (ms / 1e3) / 1e9, 1),
+                          "frac_of_hbm": round(nb / (ms / 1e3) / 1e9 / hbm_peak, 4),
+                          "rel_l2_vs_fp64": error_vs_fp64(p32, x32, y32, l, "fp32", False)}
+        del x32, y32, p32
+
+    # end to end: pinned host input -> device -> FFT -> host, every step
+    e2e_steps = max(1, min(K, 3))
+    host_in = {l: xs[l].cpu().pin_memory() for l in log2ns}
+    host_out = {l: torch.empty_like(host_in[l]).pin_memory() for l in log2ns}
+    torch.cuda.synchronize()
+    barrier(world)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(e2e_steps):
+        for l in log2ns:
+            xs[l].copy_(host_in[l], non_blocking=True)
+            plans[l].exec(xs[l], out=ys[l], stream=stream)
+            host_out[l].copy_(ys[l], non_blocking=True)
+    b.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = allreduce_max(a.elapsed_time(b), world) / e2e_steps
+    step_bytes = sum(2 * batch_for(l) * (2 << l) for l in log2ns)
+    e2e = {"value": world * transforms_per_step / (e2e_ms / 1e3), "unit": "transforms/s",
+           "h2d_bytes_per_step": step_bytes, "d2h_bytes_per_step": step_bytes, "ms_per_step": round(e2e_ms, 3),
+           "steps": e2e_steps}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(log2ns, samples_div=CPU_SAMPLE_DIV)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "transforms/s", "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f16", "data": "synthetic",
+            "config": {"workload": "fp16 dual_select forward FFT, x0.5 per pass, 1 GiB batch at each N",
+                       "N": [1 << l for l in log2ns], "batch": [batch_for(l) for l in log2ns],
+                       "precision": PRECISION, "factorization": FACTORIZATION,
+                       "input": "re/im i.i.d. uniform[-1,1], torch.Generator seeded",
+                       "l2": "inputs 1 GiB per launch > 126 MB L2; no flush", "parallelism": f"replicas{world}"},
+            "roofline": roofline, "per_n": per_n, "fp32_plain": fp32, "e2e": e2e,
+            "gpu_launches": K * sum(plans[l].info()["launches"] for l in log2ns),
+            "clocks": clocks, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+def cpu_baseline(log2ns, samples_div=CPU_SAMPLE_DIV, seconds_cap=None):
+    """Time the CPU oracle (op-by-op FP16 emulation of the same FFT) on a
+    bounded sample of each N's batch, on all host cores."""
+    import oracle as orc
+    from paper_2604_00567_b300 import signals
+    cores = os.cpu_count() or 1
+    tot_tr, tot_s = 0, 0.0
+    parts = []
+    for l in log2ns:
+        n = 1 << l
+        cnt = max(2, batch_for(l) // samples_div)
+        x = signals.signal(4242 + l, cnt, n, PRECISION)
+        t, m, p = orc.table(n, orc.DS, orc.FP16, scaled=True)
+        t0 = time.perf_counter()
+        orc.emulate_fft(x, orc.FP16, t, m, p, scaled=True, threads=cores)
+        dt = time.perf_counter() - t0
+        tot_tr += cnt
+        tot_s += dt
+        parts.append(f"{cnt}x2^{l}")
+    # the sample keeps the workload's mix (1/samples_div of each batch)
+    return {"value": tot_tr / tot_s, "unit": "transforms/s", "cores": cores, "kind": "oracle",
+            "sample": f"{', '.join(parts)} signals (1/{samples_div} of each batch), fp16 dual_select "
+                      f"op-by-op emulation in C, {tot_s:.1f} s"}
+
+
+def run_reference(args):
+    """The oracle as the reference arm: rank 0 only, bounded samples."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    log2ns = list(args.log2n)
+    vals = []
+    for _ in range(args.warmup):
+        cpu_baseline(log2ns, samples_div=CPU_SAMPLE_DIV * 8)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(log2ns, samples_div=CPU_SAMPLE_DIV * 8))
+    wall = time.perf_counter() - t0
+    value = statistics.mean(v["value"] for v in vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "transforms/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * wall / args.steps, 2),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f16",
+        "data": "synthetic",
+        "config": {"workload": "fp16 dual_select forward FFT, x0.5 per pass, 1 GiB batch at each N",
+                   "N": [1 << l for l in log2ns], "precision": PRECISION, "factorization": FACTORIZATION},
+        "cpu_baseline": {"value": value, "unit": "transforms/s", "cores": vals[0]["cores"], "kind": "oracle",
+                         "sample": vals[0]["sample"]},
+        "e2e": {"value": value, "unit": "transforms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--log2n", type=int, nargs="+", default=list(LOG2NS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,169 @@
+/*
+ * dsfft.h — C ABI of the dual-select FMA radix-2 FFT library (libdsfft.so).
+ *
+ * The library computes batched complex DFTs (Eq. 1: A = a + W b, B = a - W b,
+ * W = exp(-j 2 pi k/N)) with an m = log2 N pass radix-2 Stockham FFT
+ * (Section IV) whose butterflies are 6-FMA forms driven by a precomputed
+ * twiddle table (Sections II-III):
+ *   - dual-select (Algorithm 1): per twiddle, the cosine-outer form
+ *     (ratio tan theta, multiplier cos theta) when |cos| >= |sin|, else the
+ *     sine-outer form (ratio cot theta, multiplier sin theta); |ratio| <= 1
+ *     (Theorem 1), no clamp;
+ *   - linzer_feig_clamped (Eqs. 4-6): sine-outer everywhere, sin clamped to
+ *     -eps where |sin| < eps (the clamp practice of Section I);
+ *   - cosine (Eqs. 7-9): cosine-outer everywhere.
+ * Only the table differs between the three; the kernels are identical.
+ * Tables are computed in FP64 on the GPU and rounded once to the plan's
+ * precision.  All arithmetic of a transform runs in that precision (FP32
+ * FFMA, or packed FP16/BF16 HFMA2 on the CUDA cores).
+ *
+ * Data layout (all precisions): a batch of `batch` transforms, transform b
+ * at element offset b*N, each element an interleaved (re, im) pair:
+ *   FFT_PREC_FP32: 8 bytes  (float re, float im)      — "complex64"
+ *   FFT_PREC_FP16: 4 bytes  (half re,  half im)        — "complex-FP16"
+ *   FFT_PREC_BF16: 4 bytes  (bf16 re,  bf16 im)
+ * Output is in natural frequency order.  Pointers passed to fft_exec are
+ * device pointers (cudaMalloc or equivalent) aligned to the element size.
+ *
+ * Ownership: a plan owns its device tables; the caller owns `in`, `out` and
+ * the stream.  A plan is immutable after creation and may be used from
+ * several host threads and streams concurrently.
+ *
+ * Errors: every call returns an fft_status.  Argument and plan errors are
+ * returned synchronously and leave no work queued.  Launch failures return
+ * FFT_ERR_CUDA (the CUDA error string is available from
+ * fft_last_error_string on the calling thread).
+ */
+#ifndef DSFFT_H
+#define DSFFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum fft_status {
+    FFT_OK = 0,
+    FFT_ERR_INVALID_ARG = 1,   /* null pointer, bad enum, negative batch */
+    FFT_ERR_INVALID_SIZE = 2,  /* N not a power of two or outside [2, 2^24] */
+    FFT_ERR_UNSUPPORTED = 3,   /* valid request this build cannot run */
+    FFT_ERR_OOM = 4,           /* device allocation failed */
+    FFT_ERR_CUDA = 5,          /* a CUDA runtime call or launch failed */
+    FFT_ERR_TIMEOUT = 6        /* a bounded device-side wait gave up */
+} fft_status;
+
+typedef enum fft_precision {
+    FFT_PREC_FP32 = 0,
+    FFT_PREC_FP16 = 1,
+    FFT_PREC_BF16 = 2
+} fft_precision;
+
+typedef enum fft_factorization {
+    FFT_FAC_LINZER_FEIG_CLAMPED = 0,   /* Eqs. 4-6 with the eps clamp */
+    FFT_FAC_COSINE = 1,                /* Eqs. 7-9 */
+    FFT_FAC_DUAL_SELECT = 2            /* Algorithm 1 */
+} fft_factorization;
+
+typedef enum fft_direction {
+    FFT_FORWARD = -1,   /* W = exp(-j 2 pi k/N) (Eq. 1) */
+    FFT_INVERSE = 1     /* conjugate twiddles; unnormalised unless scaled */
+} fft_direction;
+
+typedef enum fft_scaling {
+    FFT_SCALE_NONE = 0,
+    /* exact x0.5 per pass: a' = RN(a/2), multiplier stored as RN(m/2), so the
+     * output is DFT/N.  Keeps FP16 data in range. */
+    FFT_SCALE_HALF_PER_PASS = 1
+} fft_scaling;
+
+typedef struct fft_plan_opts {
+    double lf_eps;          /* clamp for FFT_FAC_LINZER_FEIG_CLAMPED (default 1e-7) */
+    int32_t scale_forward;  /* fft_scaling of forward transforms */
+    int32_t scale_inverse;  /* fft_scaling of inverse transforms */
+    int32_t device;         /* CUDA device ordinal; -1 = current device */
+    int32_t reserved[5];    /* must be zero */
+} fft_plan_opts;
+
+typedef struct fft_plan_info {
+    int64_t n;                  /* transform length N */
+    int32_t log2n;
+    int32_t precision;          /* fft_precision */
+    int32_t factorization;      /* fft_factorization */
+    int32_t kernel;             /* 0 = fused on-chip transform, 1 = HBM sweeps */
+    int32_t launches;           /* kernel launches per fft_exec */
+    int32_t points_per_thread;  /* register block of the fused kernel */
+    int32_t threads_per_transform;
+    int32_t transforms_per_block;
+    int64_t table_bytes;        /* device bytes of the tables (both directions) */
+    int64_t element_bytes;      /* 8 (FP32) or 4 (FP16/BF16) */
+    int32_t scale_forward;
+    int32_t scale_inverse;
+    int32_t cos_count;          /* table entries on the cosine path */
+    int32_t sin_count;          /* table entries on the sine path */
+} fft_plan_info;
+
+typedef struct fft_plan fft_plan;
+
+/* Fill `opts` with the defaults for `prec`: lf_eps = 1e-7, device = -1,
+ * scale_forward = HALF_PER_PASS for FP16/BF16 and NONE for FP32,
+ * scale_inverse = NONE. */
+fft_status fft_plan_opts_init(fft_precision prec, fft_plan_opts *opts);
+
+/* Create a plan for length-N transforms (N = 2^m, 2 <= N <= 2^24).  Builds
+ * the FP64 twiddle table of Algorithm 1 (or of Eqs. 4-6 / 7-9) on the GPU
+ * for k in [0, N/2), rounds ratio and multiplier once to `prec`, and keeps
+ * the packed tables for both directions resident on the device.  Blocks
+ * until the tables are built.  `opts` may be NULL (defaults).
+ * On success *plan owns the device memory; release with fft_plan_destroy. */
+fft_status fft_plan_create(fft_plan **plan, int64_t n, fft_precision prec,
+                           fft_factorization fac, const fft_plan_opts *opts);
+
+/* Release a plan (NULL is accepted).  Work already queued that uses the plan
+ * must have completed. */
+fft_status fft_plan_destroy(fft_plan *plan);
+
+/* Transform `batch` signals (layout above) from `in` to `out`, asynchronously
+ * on `stream` (a cudaStream_t; NULL = legacy default stream).  `in` is never
+ * modified unless in == out.  in == out (in-place) is supported for
+ * N <= 2^14; larger N requires distinct buffers (FFT_ERR_UNSUPPORTED
+ * otherwise).  batch == 0 is a no-op.  Device pointers, element-aligned. */
+fft_status fft_exec(const fft_plan *plan, const void *in, void *out, int64_t batch,
+                    fft_direction dir, void *stream);
+
+/* Copy the plan's packed device table for `dir` to host memory
+ * (N/2 entries of 16 bytes; `bytes` must be at least 8*N).  Entry k:
+ *   FP32 : word0 = ratio t (float), word1 = multiplier m (float),
+ *          word2 = sigma*m (float), word3 = path (0 cosine, 1 sine)
+ *   FP16/BF16: word0 = (lo: -t, hi: t), word1 = (lo: sigma*m, hi: m),
+ *          word2 = byte-permute selector of the operand swap,
+ *          word3 = path (0 cosine, 1 sine)
+ * where sigma = +1 on the cosine path and -1 on the sine path and m already
+ * carries the x0.5 of a scaled direction.  Synchronous. */
+fft_status fft_plan_get_table(const fft_plan *plan, fft_direction dir, void *host_dst,
+                              size_t bytes);
+
+/* Describe the plan (kernel choice, launch shape, table sizes). */
+fft_status fft_plan_get_info(const fft_plan *plan, fft_plan_info *info);
+
+/* Run the FP64 stage of the table builder on the current device and return
+ * the unrounded entries for k in [0, N/2): ratio t, multiplier m (forward
+ * direction, no scaling) and path (0 cosine, 1 sine), into host arrays of
+ * N/2 elements each.  Synchronous.  Used to check the GPU's FP64
+ * trigonometry against a host evaluation. */
+fft_status fft_twiddle_fp64(int64_t n, fft_factorization fac, double lf_eps,
+                            double *host_t, double *host_m, int32_t *host_path);
+
+/* Static description of a status code. */
+const char *fft_status_string(fft_status status);
+
+/* Text of the last CUDA error seen by a library call on this host thread
+ * ("" if none). */
+const char *fft_last_error_string(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DSFFT_H */

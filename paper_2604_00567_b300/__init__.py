@@ -1,0 +1,233 @@
+"""Dual-select FMA radix-2 FFT for B300 — Python binding of ``libdsfft.so``.
+
+Argument marshalling only: every step of a transform (table build, passes)
+runs in the library's CUDA kernels.  PyTorch supplies device memory and the
+current stream.  If the shared library is missing the import of the library
+handle fails loudly — there is no CPU fallback.
+
+    import paper_2604_00567_b300 as dsfft
+    plan = dsfft.Plan(1024, "fp16", "dual_select")
+    y = plan.exec(x)                  # x: (batch, 1024, 2) float16 on cuda
+
+Storage layouts (interleaved re/im):
+    fp32 : complex64 tensor (..., N)
+    fp16 : float16 tensor  (..., N, 2)
+    bf16 : bfloat16 tensor (..., N, 2)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+__all__ = ["Plan", "lib", "twiddle_fp64", "DsfftError", "PRECISIONS", "FACTORIZATIONS",
+           "FORWARD", "INVERSE"]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdsfft.so")
+
+PRECISIONS = {"fp32": 0, "fp16": 1, "bf16": 2}
+FACTORIZATIONS = {"linzer_feig_clamped": 0, "cosine": 1, "dual_select": 2}
+FORWARD, INVERSE = -1, 1
+STATUS = {0: "FFT_OK", 1: "FFT_ERR_INVALID_ARG", 2: "FFT_ERR_INVALID_SIZE", 3: "FFT_ERR_UNSUPPORTED",
+          4: "FFT_ERR_OOM", 5: "FFT_ERR_CUDA", 6: "FFT_ERR_TIMEOUT"}
+
+
+class DsfftError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)}" + (f" ({detail})" if detail else ""))
+
+
+class PlanOpts(ctypes.Structure):
+    _fields_ = [("lf_eps", ctypes.c_double), ("scale_forward", ctypes.c_int32),
+                ("scale_inverse", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("log2n", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("factorization", ctypes.c_int32), ("kernel", ctypes.c_int32),
+                ("launches", ctypes.c_int32), ("points_per_thread", ctypes.c_int32),
+                ("threads_per_transform", ctypes.c_int32), ("transforms_per_block", ctypes.c_int32),
+                ("table_bytes", ctypes.c_int64), ("element_bytes", ctypes.c_int64),
+                ("scale_forward", ctypes.c_int32), ("scale_inverse", ctypes.c_int32),
+                ("cos_count", ctypes.c_int32), ("sin_count", ctypes.c_int32)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """Load ``libdsfft.so`` (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libdsfft.so not found at {LIB_PATH}; build it with "
+                                   "`python -m paper_2604_00567_b300.build`")
+            L = ctypes.CDLL(LIB_PATH)
+            P, i32, i64, d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+            L.fft_plan_opts_init.argtypes = [i32, ctypes.POINTER(PlanOpts)]
+            L.fft_plan_create.argtypes = [ctypes.POINTER(P), i64, i32, i32, ctypes.POINTER(PlanOpts)]
+            L.fft_plan_destroy.argtypes = [P]
+            L.fft_exec.argtypes = [P, P, P, i64, i32, P]
+            L.fft_plan_get_table.argtypes = [P, i32, P, ctypes.c_size_t]
+            L.fft_plan_get_info.argtypes = [P, ctypes.POINTER(PlanInfo)]
+            L.fft_twiddle_fp64.argtypes = [i64, i32, d, P, P, P]
+            L.fft_status_string.restype = ctypes.c_char_p
+            L.fft_status_string.argtypes = [i32]
+            L.fft_last_error_string.restype = ctypes.c_char_p
+            L.fft_last_error_string.argtypes = []
+            for name in ("fft_plan_opts_init", "fft_plan_create", "fft_plan_destroy", "fft_exec",
+                         "fft_plan_get_table", "fft_plan_get_info", "fft_twiddle_fp64"):
+                getattr(L, name).restype = i32
+            _lib = L
+    return _lib
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise DsfftError(status, where, lib().fft_last_error_string().decode())
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Plan:
+    """A resident FFT plan: length ``n``, precision and factorization."""
+
+    def __init__(self, n: int, precision: str = "fp32", factorization: str = "dual_select",
+                 lf_eps: float = 1e-7, scale_forward: bool | None = None,
+                 scale_inverse: bool | None = None, device: int | None = None):
+        L = lib()
+        self.n = int(n)
+        self.precision = precision
+        self.factorization = factorization
+        opts = PlanOpts()
+        _check(L.fft_plan_opts_init(PRECISIONS[precision], ctypes.byref(opts)), "fft_plan_opts_init")
+        opts.lf_eps = float(lf_eps)
+        if scale_forward is not None:
+            opts.scale_forward = 1 if scale_forward else 0
+        if scale_inverse is not None:
+            opts.scale_inverse = 1 if scale_inverse else 0
+        if device is not None:
+            opts.device = int(device)
+        self.scale_forward = bool(opts.scale_forward)
+        self.scale_inverse = bool(opts.scale_inverse)
+        h = ctypes.c_void_p()
+        _check(L.fft_plan_create(ctypes.byref(h), self.n, PRECISIONS[precision],
+                                 FACTORIZATIONS[factorization], ctypes.byref(opts)),
+               f"fft_plan_create(N={n}, {precision}, {factorization})")
+        self._h = h
+
+    # ------------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().fft_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        return self._h
+
+    def info(self) -> dict:
+        inf = PlanInfo()
+        _check(lib().fft_plan_get_info(self._h, ctypes.byref(inf)), "fft_plan_get_info")
+        return {k: getattr(inf, k) for k, _ in PlanInfo._fields_}
+
+    def element_bytes(self) -> int:
+        return 8 if self.precision == "fp32" else 4
+
+    def _check_tensor(self, x, name):
+        import torch
+        if not x.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if not x.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if self.precision == "fp32":
+            if x.dtype != torch.complex64 or x.shape[-1] != self.n:
+                raise ValueError(f"{name}: expected complex64 (..., {self.n}), got {x.dtype} {tuple(x.shape)}")
+            return x.numel() // self.n
+        want = torch.float16 if self.precision == "fp16" else torch.bfloat16
+        if x.dtype != want or x.shape[-2:] != (self.n, 2):
+            raise ValueError(f"{name}: expected {want} (..., {self.n}, 2), got {x.dtype} {tuple(x.shape)}")
+        return x.numel() // (2 * self.n)
+
+    def exec(self, x, direction: int = FORWARD, out=None, stream=None):
+        """Transform every signal of ``x`` (see module docstring for layouts)
+        on ``stream`` (default: torch's current stream).  Returns ``out``."""
+        import torch
+        batch = self._check_tensor(x, "x")
+        if out is None:
+            out = torch.empty_like(x)
+        elif self._check_tensor(out, "out") != batch or out.shape != x.shape:
+            raise ValueError("out must have the shape of x")
+        _check(lib().fft_exec(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                              batch, int(direction), _stream_handle(stream)), "fft_exec")
+        return out
+
+    def exec_ptr(self, in_ptr: int, out_ptr: int, batch: int, direction: int = FORWARD,
+                 stream_handle: int = 0):
+        """Raw-pointer form of :meth:`exec` (device pointers, cudaStream_t)."""
+        _check(lib().fft_exec(self._h, ctypes.c_void_p(in_ptr), ctypes.c_void_p(out_ptr), int(batch),
+                              int(direction), ctypes.c_void_p(stream_handle)), "fft_exec")
+
+    def raw_table(self, direction: int = FORWARD) -> np.ndarray:
+        """The packed device table for ``direction`` as a (N/2, 4) uint32 array."""
+        h = self.n // 2
+        buf = np.empty((h, 4), dtype=np.uint32)
+        _check(lib().fft_plan_get_table(self._h, int(direction), buf.ctypes.data_as(ctypes.c_void_p),
+                                        buf.nbytes), "fft_plan_get_table")
+        return buf
+
+    def table(self, direction: int = FORWARD):
+        """Decode the packed table: ``(t, m, path)`` as float64/float64/int32
+        arrays (m includes the x0.5 of a scaled direction)."""
+        raw = self.raw_table(direction)
+        path = raw[:, 3].astype(np.int32)
+        if self.precision == "fp32":
+            t = raw[:, 0].view(np.float32).astype(np.float64)
+            m = raw[:, 1].view(np.float32).astype(np.float64)
+        else:
+            thi = (raw[:, 0] >> 16).astype(np.uint16)
+            mhi = (raw[:, 1] >> 16).astype(np.uint16)
+            if self.precision == "fp16":
+                t = thi.view(np.float16).astype(np.float64)
+                m = mhi.view(np.float16).astype(np.float64)
+            else:
+                t = (thi.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+                m = (mhi.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+        return t, m, path
+
+
+def twiddle_fp64(n: int, factorization: str = "dual_select", lf_eps: float = 1e-7):
+    """The GPU's FP64 table stage (before rounding), forward direction:
+    ``(t, m, path)`` for k in [0, n/2)."""
+    h = int(n) // 2
+    t = np.empty(h, dtype=np.float64)
+    m = np.empty(h, dtype=np.float64)
+    p = np.empty(h, dtype=np.int32)
+    _check(lib().fft_twiddle_fp64(int(n), FACTORIZATIONS[factorization], float(lf_eps),
+                                  t.ctypes.data_as(ctypes.c_void_p), m.ctypes.data_as(ctypes.c_void_p),
+                                  p.ctypes.data_as(ctypes.c_void_p)), "fft_twiddle_fp64")
+    return t, m, p

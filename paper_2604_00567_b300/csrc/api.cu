@@ -1,0 +1,255 @@
+// api.cu — the C ABI of libdsfft (declared in include/dsfft.h): plan
+// creation (FP64 table build on the GPU, rounding once, resident packed
+// tables for both directions), execution dispatch and error reporting.
+#include <stdio.h>
+#include <string.h>
+
+#include "../../include/dsfft.h"
+#include "internal.h"
+
+using namespace dsfft;
+
+struct fft_plan {
+  int64_t n;
+  int log2n;
+  int prec;
+  int fac;
+  double eps;
+  int scale[2];         // [0] forward, [1] inverse
+  int device;
+  uint4 *table[2];      // packed tables, [0] forward, [1] inverse
+  int kernel;           // 0 fused
+  FusedShape shape;
+  int cos_count, sin_count;
+};
+
+namespace {
+
+thread_local char g_last_error[256] = "";
+
+fft_status cuda_fail(cudaError_t e, const char *where) {
+  snprintf(g_last_error, sizeof g_last_error, "%s: %s", where, cudaGetErrorString(e));
+  if (e == cudaErrorMemoryAllocation) return FFT_ERR_OOM;
+  return FFT_ERR_CUDA;
+}
+
+// Make `device` current for the lifetime of the guard (device < 0 keeps the
+// caller's current device), restoring the caller's device afterwards.
+struct DeviceGuard {
+  int prev = -1;
+  bool switched = false;
+  cudaError_t err = cudaSuccess;
+  explicit DeviceGuard(int device) {
+    if (device < 0) return;
+    err = cudaGetDevice(&prev);
+    if (err != cudaSuccess) return;
+    if (prev != device) {
+      err = cudaSetDevice(device);
+      switched = err == cudaSuccess;
+    }
+  }
+  ~DeviceGuard() {
+    if (switched) cudaSetDevice(prev);
+  }
+};
+
+int ilog2_exact(int64_t n) {
+  if (n < 2 || (n & (n - 1)) != 0) return -1;
+  int l = 0;
+  while ((1LL << l) < n) ++l;
+  return l;
+}
+
+size_t elem_bytes(int prec) { return prec == kFP32 ? 8 : 4; }
+
+}  // namespace
+
+extern "C" {
+
+const char *fft_status_string(fft_status s) {
+  switch (s) {
+    case FFT_OK: return "ok";
+    case FFT_ERR_INVALID_ARG: return "invalid argument";
+    case FFT_ERR_INVALID_SIZE: return "invalid size (N must be a power of two in [2, 2^24])";
+    case FFT_ERR_UNSUPPORTED: return "unsupported request";
+    case FFT_ERR_OOM: return "device out of memory";
+    case FFT_ERR_CUDA: return "CUDA error";
+    case FFT_ERR_TIMEOUT: return "device-side wait timed out";
+  }
+  return "unknown status";
+}
+
+const char *fft_last_error_string(void) { return g_last_error; }
+
+fft_status fft_plan_opts_init(fft_precision prec, fft_plan_opts *opts) {
+  if (!opts) return FFT_ERR_INVALID_ARG;
+  if (prec != FFT_PREC_FP32 && prec != FFT_PREC_FP16 && prec != FFT_PREC_BF16) return FFT_ERR_INVALID_ARG;
+  memset(opts, 0, sizeof *opts);
+  opts->lf_eps = 1e-7;
+  opts->scale_forward = prec == FFT_PREC_FP32 ? FFT_SCALE_NONE : FFT_SCALE_HALF_PER_PASS;
+  opts->scale_inverse = FFT_SCALE_NONE;
+  opts->device = -1;
+  return FFT_OK;
+}
+
+fft_status fft_plan_create(fft_plan **plan, int64_t n, fft_precision prec, fft_factorization fac,
+                           const fft_plan_opts *opts_in) {
+  if (!plan) return FFT_ERR_INVALID_ARG;
+  *plan = nullptr;
+  if (prec != FFT_PREC_FP32 && prec != FFT_PREC_FP16 && prec != FFT_PREC_BF16) return FFT_ERR_INVALID_ARG;
+  if (fac != FFT_FAC_LINZER_FEIG_CLAMPED && fac != FFT_FAC_COSINE && fac != FFT_FAC_DUAL_SELECT)
+    return FFT_ERR_INVALID_ARG;
+  fft_plan_opts opts;
+  fft_plan_opts_init(prec, &opts);
+  if (opts_in) {
+    opts = *opts_in;
+    for (int r : opts.reserved)
+      if (r != 0) return FFT_ERR_INVALID_ARG;
+  }
+  if (!(opts.lf_eps > 0.0) || !(opts.lf_eps < 1.0)) return FFT_ERR_INVALID_ARG;
+  for (int s : {opts.scale_forward, opts.scale_inverse})
+    if (s != FFT_SCALE_NONE && s != FFT_SCALE_HALF_PER_PASS) return FFT_ERR_INVALID_ARG;
+  const int log2n = ilog2_exact(n);
+  if (log2n < 1 || log2n > kMaxLog2N) return FFT_ERR_INVALID_SIZE;
+  if (log2n > kFusedMaxLog2N) {
+    snprintf(g_last_error, sizeof g_last_error, "N = 2^%d needs the multi-sweep path", log2n);
+    return FFT_ERR_UNSUPPORTED;
+  }
+
+  DeviceGuard guard(opts.device);
+  if (guard.err != cudaSuccess) return cuda_fail(guard.err, "select device");
+  int device = 0;
+  cudaError_t e = cudaGetDevice(&device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+
+  fft_plan *p = new fft_plan();
+  p->n = n;
+  p->log2n = log2n;
+  p->prec = prec;
+  p->fac = fac;
+  p->eps = opts.lf_eps;
+  p->scale[0] = opts.scale_forward;
+  p->scale[1] = opts.scale_inverse;
+  p->device = device;
+  p->kernel = 0;
+  p->shape = fused_shape(prec, log2n);
+
+  const size_t entries = (size_t)(n / 2);
+  int *counts = nullptr;
+  cudaStream_t st = nullptr;
+  fft_status status = FFT_OK;
+  int host_counts[2] = {0, 0};
+  do {
+    if ((e = cudaMalloc(&p->table[0], entries * sizeof(uint4))) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc table"); break; }
+    if ((e = cudaMalloc(&p->table[1], entries * sizeof(uint4))) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc table"); break; }
+    if ((e = cudaMalloc(&counts, 2 * sizeof(int))) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc counts"); break; }
+    if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) { status = cuda_fail(e, "stream"); break; }
+    if ((e = cudaMemsetAsync(counts, 0, 2 * sizeof(int), st)) != cudaSuccess) { status = cuda_fail(e, "memset"); break; }
+    if ((e = launch_build_table(log2n, fac, opts.lf_eps, prec, 0, p->scale[0], p->table[0], counts, st)) != cudaSuccess) { status = cuda_fail(e, "table build"); break; }
+    if ((e = launch_build_table(log2n, fac, opts.lf_eps, prec, 1, p->scale[1], p->table[1], nullptr, st)) != cudaSuccess) { status = cuda_fail(e, "table build"); break; }
+    if ((e = cudaMemcpyAsync(host_counts, counts, 2 * sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess) { status = cuda_fail(e, "copy counts"); break; }
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) { status = cuda_fail(e, "table build sync"); break; }
+    if ((e = prepare_fused(prec, log2n)) != cudaSuccess) { status = cuda_fail(e, "kernel attributes"); break; }
+  } while (0);
+  if (st) cudaStreamDestroy(st);
+  if (counts) cudaFree(counts);
+  if (status != FFT_OK) {
+    if (p->table[0]) cudaFree(p->table[0]);
+    if (p->table[1]) cudaFree(p->table[1]);
+    delete p;
+    return status;
+  }
+  p->cos_count = host_counts[0];
+  p->sin_count = host_counts[1];
+  *plan = p;
+  return FFT_OK;
+}
+
+fft_status fft_plan_destroy(fft_plan *plan) {
+  if (!plan) return FFT_OK;
+  DeviceGuard guard(plan->device);
+  if (plan->table[0]) cudaFree(plan->table[0]);
+  if (plan->table[1]) cudaFree(plan->table[1]);
+  delete plan;
+  return FFT_OK;
+}
+
+fft_status fft_exec(const fft_plan *plan, const void *in, void *out, int64_t batch, fft_direction dir,
+                    void *stream) {
+  if (!plan) return FFT_ERR_INVALID_ARG;
+  if (dir != FFT_FORWARD && dir != FFT_INVERSE) return FFT_ERR_INVALID_ARG;
+  if (batch < 0) return FFT_ERR_INVALID_ARG;
+  if (batch == 0) return FFT_OK;
+  if (!in || !out) return FFT_ERR_INVALID_ARG;
+  const size_t eb = elem_bytes(plan->prec);
+  if (((uintptr_t)in % eb) != 0 || ((uintptr_t)out % eb) != 0) return FFT_ERR_INVALID_ARG;
+  const int d = dir == FFT_FORWARD ? 0 : 1;
+  DeviceGuard guard(plan->device);
+  if (guard.err != cudaSuccess) return cuda_fail(guard.err, "select device");
+  cudaError_t e = launch_fused(plan->prec, plan->log2n, plan->scale[d] != 0, in, out, batch, plan->table[d],
+                               (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "fused kernel launch");
+  return FFT_OK;
+}
+
+fft_status fft_plan_get_table(const fft_plan *plan, fft_direction dir, void *host_dst, size_t bytes) {
+  if (!plan || !host_dst) return FFT_ERR_INVALID_ARG;
+  if (dir != FFT_FORWARD && dir != FFT_INVERSE) return FFT_ERR_INVALID_ARG;
+  const size_t need = (size_t)(plan->n / 2) * sizeof(uint4);
+  if (bytes < need) return FFT_ERR_INVALID_ARG;
+  DeviceGuard guard(plan->device);
+  cudaError_t e = cudaMemcpy(host_dst, plan->table[dir == FFT_FORWARD ? 0 : 1], need, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "copy table");
+  return FFT_OK;
+}
+
+fft_status fft_plan_get_info(const fft_plan *plan, fft_plan_info *info) {
+  if (!plan || !info) return FFT_ERR_INVALID_ARG;
+  memset(info, 0, sizeof *info);
+  info->n = plan->n;
+  info->log2n = plan->log2n;
+  info->precision = plan->prec;
+  info->factorization = plan->fac;
+  info->kernel = plan->kernel;
+  info->launches = 1;
+  info->points_per_thread = 1 << plan->shape.log2r;
+  info->threads_per_transform = plan->shape.threads_per_transform;
+  info->transforms_per_block = plan->shape.transforms_per_block;
+  info->table_bytes = (int64_t)2 * (plan->n / 2) * (int64_t)sizeof(uint4);
+  info->element_bytes = (int64_t)elem_bytes(plan->prec);
+  info->scale_forward = plan->scale[0];
+  info->scale_inverse = plan->scale[1];
+  info->cos_count = plan->cos_count;
+  info->sin_count = plan->sin_count;
+  return FFT_OK;
+}
+
+fft_status fft_twiddle_fp64(int64_t n, fft_factorization fac, double lf_eps, double *host_t, double *host_m,
+                            int32_t *host_path) {
+  if (!host_t || !host_m || !host_path) return FFT_ERR_INVALID_ARG;
+  if (fac != FFT_FAC_LINZER_FEIG_CLAMPED && fac != FFT_FAC_COSINE && fac != FFT_FAC_DUAL_SELECT)
+    return FFT_ERR_INVALID_ARG;
+  if (!(lf_eps > 0.0) || !(lf_eps < 1.0)) return FFT_ERR_INVALID_ARG;
+  const int log2n = ilog2_exact(n);
+  if (log2n < 1 || log2n > kMaxLog2N) return FFT_ERR_INVALID_SIZE;
+  const size_t h = (size_t)(n / 2);
+  double *t = nullptr, *m = nullptr;
+  int *path = nullptr;
+  fft_status status = FFT_OK;
+  cudaError_t e;
+  do {
+    if ((e = cudaMalloc(&t, h * sizeof(double))) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc"); break; }
+    if ((e = cudaMalloc(&m, h * sizeof(double))) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc"); break; }
+    if ((e = cudaMalloc(&path, h * sizeof(int))) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc"); break; }
+    if ((e = launch_fp64_table(log2n, fac, lf_eps, t, m, path, nullptr)) != cudaSuccess) { status = cuda_fail(e, "fp64 table"); break; }
+    if ((e = cudaMemcpy(host_t, t, h * sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess) { status = cuda_fail(e, "copy"); break; }
+    if ((e = cudaMemcpy(host_m, m, h * sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess) { status = cuda_fail(e, "copy"); break; }
+    if ((e = cudaMemcpy(host_path, path, h * sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess) { status = cuda_fail(e, "copy"); break; }
+  } while (0);
+  if (t) cudaFree(t);
+  if (m) cudaFree(m);
+  if (path) cudaFree(path);
+  return status;
+}
+
+}  // extern "C"

@@ -1,0 +1,202 @@
+// fused.cu — one-launch FFT for N <= 2^14: every pass of a transform runs on
+// chip, so each signal is read from HBM once and written once.
+//
+// The m = log2 N radix-2 Stockham passes (Section IV) are grouped into
+// stages of up to r = log2 R passes.  Before pass P the Stockham array is
+// Z_P[s 2^P + j] (s in [0, N/2^P), j in [0, 2^P)); pass P combines
+// a = Z_P[s 2^P + j], b = Z_P[N/2 + s 2^P + j] with W = table[j N/2^(P+1)]
+// into Z_{P+1}[s 2^(P+1) + j] = a + W b, Z_{P+1}[s 2^(P+1) + 2^P + j] = a - W b.
+// A stage of rho passes starting at P only mixes, for each (s_lo, j), the
+// 2^rho values Z_P[(s_lo + q N/2^(P+rho)) 2^P + j], q in [0, 2^rho), so one
+// thread keeps them in registers and runs the rho passes with the exact
+// butterflies of the radix-2 algorithm (same operands, same twiddles, same
+// rounding): the result is bit-identical to pass-by-pass execution.  Stages
+// exchange data through shared memory.  Thread `tid` of a transform reads
+// Z_P[tid + p T] (p in [0, R), T = N/R threads), which is coalesced for the
+// first stage (from HBM) and bank-conflict-free for the others; the last
+// stage writes X[tid + p T] (coalesced).
+#include "common.cuh"
+#include "internal.h"
+
+namespace dsfft {
+
+template <int PREC, int LOG2N, int LOG2R, bool SCALED>
+struct Fused {
+  using E = typename Elem<PREC>::T;
+  static constexpr int N = 1 << LOG2N;
+  static constexpr int R = 1 << LOG2R;
+  static constexpr int T = N / R;                        // threads per transform
+  static constexpr int TPC = T >= 256 ? 1 : 256 / T;     // transforms per block
+  static constexpr int TPB = T * TPC;
+  static constexpr int NSTAGES = (LOG2N + LOG2R - 1) / LOG2R;
+  static constexpr int PADN = N + (N >> 5);              // one pad element per 32
+  static constexpr int SMEM = NSTAGES > 1 ? TPC * PADN * (int)sizeof(E) : 0;
+
+  static __device__ __forceinline__ int pad(int idx) { return idx + (idx >> 5); }
+
+  // rho radix-2 passes starting at pass P on the registers of one thread.
+  template <int P, int RHO>
+  static __device__ __forceinline__ void compute(E (&v)[R], int tid, const uint4 *__restrict__ tw) {
+    constexpr int C = R >> RHO;   // independent groups per thread
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const int g = tid + c * T;
+      const int j = g & ((1 << P) - 1);
+#pragma unroll
+      for (int i = 0; i < RHO; ++i) {
+        const int half = 1 << (RHO - 1 - i);
+#pragma unroll
+        for (int ql = 0; ql < (1 << i); ++ql) {
+          const int k = (j + (ql << P)) << (LOG2N - P - i - 1);
+          const uint4 e = __ldg(tw + k);
+          const int qtop = bitrev(ql, i) << (RHO - i);
+#pragma unroll
+          for (int qh = 0; qh < half; ++qh) {
+            const int q = qtop | qh;
+            Bfly<PREC, SCALED>::run(v[c + q * C], v[c + (q + half) * C], e);
+          }
+        }
+      }
+    }
+  }
+
+  template <int S>
+  static __device__ __forceinline__ void stages(E (&v)[R], E *sm, int tid, const uint4 *__restrict__ tw,
+                                                E *dst, bool active) {
+    constexpr int P = S * LOG2R;
+    constexpr int RHO = (LOG2N - P) < LOG2R ? (LOG2N - P) : LOG2R;
+    constexpr int C = R >> RHO;
+    if constexpr (S > 0) {
+#pragma unroll
+      for (int p = 0; p < R; ++p) v[p] = sm[pad(tid + p * T)];
+    }
+    compute<P, RHO>(v, tid, tw);
+    if constexpr (P + RHO == LOG2N) {
+      if (active) {
+#pragma unroll
+        for (int c = 0; c < C; ++c)
+#pragma unroll
+          for (int q = 0; q < (1 << RHO); ++q)
+            dst[tid + c * T + (bitrev(q, RHO) << P)] = v[c + q * C];
+      }
+    } else {
+      if constexpr (S > 0) __syncthreads();   // previous exchange fully read
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const int g = tid + c * T;
+        const int base = ((g >> P) << (P + RHO)) + (g & ((1 << P) - 1));
+#pragma unroll
+        for (int q = 0; q < (1 << RHO); ++q) sm[pad(base + (bitrev(q, RHO) << P))] = v[c + q * C];
+      }
+      __syncthreads();
+      stages<S + 1>(v, sm, tid, tw, dst, active);
+    }
+  }
+};
+
+template <int PREC, int LOG2N, int LOG2R, bool SCALED>
+__global__ void __launch_bounds__(Fused<PREC, LOG2N, LOG2R, SCALED>::TPB)
+    fused_fft_kernel(const typename Elem<PREC>::T *in, typename Elem<PREC>::T *out, int64_t batch,
+                     const uint4 *__restrict__ tw) {
+  using K = Fused<PREC, LOG2N, LOG2R, SCALED>;
+  using E = typename K::E;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lt = threadIdx.x / K::T;
+  const int tid = threadIdx.x % K::T;
+  const int64_t tr = (int64_t)blockIdx.x * K::TPC + lt;
+  const bool active = tr < batch;
+  E *sm = reinterpret_cast<E *>(smem_raw) + lt * K::PADN;
+  E v[K::R];
+  const E *src = in + tr * K::N;
+  if (active) {
+#pragma unroll
+    for (int p = 0; p < K::R; ++p) v[p] = src[tid + p * K::T];
+  } else {
+#pragma unroll
+    for (int p = 0; p < K::R; ++p) v[p] = E{};
+  }
+  K::template stages<0>(v, sm, tid, tw, out + tr * K::N, active);
+}
+
+// ---------------------------------------------------------------------------
+// dispatch
+
+constexpr int fused_log2r(int prec, int log2n) {
+  (void)prec;
+  return log2n < 4 ? log2n : 4;
+}
+
+template <int PREC, int LOG2N, bool SCALED>
+static cudaError_t launch_one(const void *in, void *out, int64_t batch, const uint4 *tw, cudaStream_t stream) {
+  constexpr int LOG2R = fused_log2r(PREC, LOG2N);
+  using K = Fused<PREC, LOG2N, LOG2R, SCALED>;
+  using E = typename K::E;
+  auto kern = fused_fft_kernel<PREC, LOG2N, LOG2R, SCALED>;
+  const int64_t blocks = (batch + K::TPC - 1) / K::TPC;
+  if (blocks > 0x7FFFFFFF) return cudaErrorInvalidConfiguration;
+  kern<<<(unsigned)blocks, K::TPB, K::SMEM, stream>>>(static_cast<const E *>(in), static_cast<E *>(out), batch, tw);
+  return cudaGetLastError();
+}
+
+// Raise the dynamic shared-memory limit of both variants on the current
+// device (needed above 48 KB); called once per plan creation.
+template <int PREC, int LOG2N>
+static cudaError_t prepare_one() {
+  constexpr int LOG2R = fused_log2r(PREC, LOG2N);
+  using K = Fused<PREC, LOG2N, LOG2R, false>;
+  if (K::SMEM <= 48 * 1024) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(fused_fft_kernel<PREC, LOG2N, LOG2R, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(fused_fft_kernel<PREC, LOG2N, LOG2R, true>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM);
+}
+
+template <int PREC, int LOG2N>
+static FusedShape shape_one() {
+  constexpr int LOG2R = fused_log2r(PREC, LOG2N);
+  using K = Fused<PREC, LOG2N, LOG2R, false>;
+  return FusedShape{LOG2R, K::T, K::TPC, K::TPB, K::SMEM};
+}
+
+using LaunchFn = cudaError_t (*)(const void *, void *, int64_t, const uint4 *, cudaStream_t);
+using ShapeFn = FusedShape (*)();
+using PrepareFn = cudaError_t (*)();
+
+template <int PREC, int... L>
+struct Table {
+  static constexpr LaunchFn plain[] = {launch_one<PREC, L, false>...};
+  static constexpr LaunchFn scaled[] = {launch_one<PREC, L, true>...};
+  static constexpr ShapeFn shape[] = {shape_one<PREC, L>...};
+  static constexpr PrepareFn prepare[] = {prepare_one<PREC, L>...};
+};
+
+#define DSFFT_LOG2N_LIST 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14
+using T32 = Table<kFP32, DSFFT_LOG2N_LIST>;
+using T16 = Table<kFP16, DSFFT_LOG2N_LIST>;
+using TB16 = Table<kBF16, DSFFT_LOG2N_LIST>;
+
+FusedShape fused_shape(int prec, int log2n) {
+  if (log2n < 1 || log2n > kFusedMaxLog2N) return FusedShape{0, 0, 0, 0, 0};
+  const int i = log2n - 1;
+  return prec == kFP32 ? T32::shape[i]() : prec == kFP16 ? T16::shape[i]() : TB16::shape[i]();
+}
+
+cudaError_t prepare_fused(int prec, int log2n) {
+  if (log2n < 1 || log2n > kFusedMaxLog2N) return cudaErrorInvalidValue;
+  const int i = log2n - 1;
+  return prec == kFP32 ? T32::prepare[i]() : prec == kFP16 ? T16::prepare[i]() : TB16::prepare[i]();
+}
+
+cudaError_t launch_fused(int prec, int log2n, bool scaled, const void *in, void *out, int64_t batch,
+                         const uint4 *table, cudaStream_t stream) {
+  if (log2n < 1 || log2n > kFusedMaxLog2N) return cudaErrorInvalidValue;
+  const int i = log2n - 1;
+  LaunchFn f;
+  if (prec == kFP32) f = scaled ? T32::scaled[i] : T32::plain[i];
+  else if (prec == kFP16) f = scaled ? T16::scaled[i] : T16::plain[i];
+  else f = scaled ? TB16::scaled[i] : TB16::plain[i];
+  return f(in, out, batch, table, stream);
+}
+
+}  // namespace dsfft

@@ -1,0 +1,36 @@
+// internal.h — host-side declarations shared by the library's translation
+// units (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dsfft {
+
+enum Prec : int { kFP32 = 0, kFP16 = 1, kBF16 = 2 };
+
+constexpr int kMaxLog2N = 24;
+constexpr int kFusedMaxLog2N = 14;   // whole transform staged on chip
+
+cudaError_t launch_build_table(int log2n, int fac, double eps, int prec, int inverse, int scaled,
+                               uint4 *out, int *counts, cudaStream_t stream);
+cudaError_t launch_fp64_table(int log2n, int fac, double eps, double *t, double *m, int *path,
+                              cudaStream_t stream);
+
+// Shape of the fused kernel for (prec, log2n).
+struct FusedShape {
+  int log2r;                 // points per thread = 2^log2r
+  int threads_per_transform;
+  int transforms_per_block;
+  int threads_per_block;
+  int smem_bytes;
+};
+FusedShape fused_shape(int prec, int log2n);
+
+cudaError_t prepare_fused(int prec, int log2n);
+
+// Fused on-chip transform of `batch` signals of length 2^log2n.
+cudaError_t launch_fused(int prec, int log2n, bool scaled, const void *in, void *out, int64_t batch,
+                         const uint4 *table, cudaStream_t stream);
+
+}  // namespace dsfft

@@ -1,0 +1,117 @@
+// table.cu — FP64 twiddle-table builder (Algorithm 1 and the two single
+// factorizations of Eqs. 4-6 and 7-9), run on the GPU once per plan.
+//
+// For k in [0, N/2): theta = (-2 pi k)/N in FP64 (evaluated in that order,
+// so the entries of N are every (Nmax/N)-th entry of the table of Nmax),
+// w_r = cos theta, w_i = sin theta.  Selection:
+//   dual-select : cosine path when |w_r| >= |w_i| (Algorithm 1), else sine
+//   linzer-feig : sine path; w_i := -eps where |w_i| < eps (Section I clamp)
+//   cosine      : cosine path
+// cosine path: m = w_r, t = w_i / w_r ; sine path: m = w_i, t = w_r / w_i.
+// The inverse direction conjugates W (w_i -> -w_i) after the clamp; a scaled
+// direction stores m/2.  t and m are then rounded ONCE (cvt.rn) from FP64
+// to the plan precision and packed (layout in common.cuh).
+#include "common.cuh"
+#include "internal.h"
+
+namespace dsfft {
+
+__device__ __forceinline__ uint16_t f64_to_f16_bits(double x) {
+  uint16_t h;
+  asm("cvt.rn.f16.f64 %0, %1;" : "=h"(h) : "d"(x));
+  return h;
+}
+__device__ __forceinline__ uint16_t f64_to_bf16_bits(double x) {
+  uint16_t h;
+  asm("cvt.rn.bf16.f64 %0, %1;" : "=h"(h) : "d"(x));
+  return h;
+}
+
+struct Fp64Entry {
+  double t, m;
+  int sine;
+};
+
+__device__ __forceinline__ Fp64Entry fp64_entry(int64_t k, int log2n, int fac, double eps, int inverse) {
+  const double th = (-kTwoPi * (double)k) / (double)(1LL << log2n);
+  double wr, wi;
+  sincos(th, &wi, &wr);
+  int sine;
+  if (fac == 2) {
+    sine = !(fabs(wr) >= fabs(wi));
+  } else if (fac == 0) {
+    sine = 1;
+    if (fabs(wi) < eps) wi = -eps;
+  } else {
+    sine = 0;
+  }
+  if (inverse) wi = -wi;
+  Fp64Entry e;
+  if (sine) {
+    e.m = wi;
+    e.t = wr / wi;
+  } else {
+    e.m = wr;
+    e.t = wi / wr;
+  }
+  e.sine = sine;
+  return e;
+}
+
+__global__ void build_table_kernel(int log2n, int fac, double eps, int prec, int inverse, int scaled,
+                                   uint4 *__restrict__ out, int *__restrict__ counts) {
+  const int64_t half = 1LL << (log2n - 1);
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= half) return;
+  Fp64Entry e = fp64_entry(k, log2n, fac, eps, inverse);
+  double m = scaled ? e.m * 0.5 : e.m;   // exact scaling by a power of two
+  uint4 w;
+  if (prec == kFP32) {
+    const float tf = __double2float_rn(e.t);
+    const float mf = __double2float_rn(m);
+    w.x = __float_as_uint(tf);
+    w.y = __float_as_uint(mf);
+    w.z = __float_as_uint(e.sine ? -mf : mf);
+    w.w = (uint32_t)e.sine;
+  } else {
+    const uint32_t tb = prec == kFP16 ? f64_to_f16_bits(e.t) : f64_to_bf16_bits(e.t);
+    const uint32_t mb = prec == kFP16 ? f64_to_f16_bits(m) : f64_to_bf16_bits(m);
+    const uint32_t smb = e.sine ? (mb ^ 0x8000u) : mb;
+    w.x = ((tb ^ 0x8000u) & 0xFFFFu) | (tb << 16);        // (lo -t, hi t)
+    w.y = (smb & 0xFFFFu) | (mb << 16);                   // (lo sigma*m, hi m)
+    w.z = e.sine ? 0x3210u : 0x1032u;                     // X = cosine ? swap(b) : b
+    w.w = (uint32_t)e.sine;
+  }
+  out[k] = w;
+  if (counts) atomicAdd(&counts[e.sine], 1);
+}
+
+__global__ void fp64_table_kernel(int log2n, int fac, double eps, double *t, double *m, int *path) {
+  const int64_t half = 1LL << (log2n - 1);
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= half) return;
+  Fp64Entry e = fp64_entry(k, log2n, fac, eps, 0);
+  t[k] = e.t;
+  m[k] = e.m;
+  path[k] = e.sine;
+}
+
+cudaError_t launch_build_table(int log2n, int fac, double eps, int prec, int inverse, int scaled,
+                               uint4 *out, int *counts, cudaStream_t stream) {
+  const int64_t half = 1LL << (log2n - 1);
+  const int threads = 256;
+  const unsigned blocks = (unsigned)((half + threads - 1) / threads);
+  build_table_kernel<<<blocks, threads, 0, stream>>>(log2n, fac, eps, prec, inverse, scaled, out, counts);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fp64_table(int log2n, int fac, double eps, double *t, double *m, int *path,
+                              cudaStream_t stream) {
+  const int64_t half = 1LL << (log2n - 1);
+  const int threads = 256;
+  const unsigned blocks = (unsigned)((half + threads - 1) / threads);
+  fp64_table_kernel<<<blocks, threads, 0, stream>>>(log2n, fac, eps, t, m, path);
+  return cudaGetLastError();
+}
+
+}  // namespace dsfft

@@ -1,0 +1,94 @@
+"""The C-ABI library builds, loads without a GPU, exports every function that
+include/*.h declares, and validates arguments on the host (no CUDA calls)."""
+import ctypes
+import glob
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        for m in re.finditer(r"\b(fft_\w+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2604_00567_b300 import build
+    build.build()
+    import paper_2604_00567_b300 as dsfft
+    return dsfft.lib()
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("fft_plan_create", "fft_exec", "fft_plan_destroy", "fft_plan_get_table",
+                     "fft_plan_get_info", "fft_status_string"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2604_00567_b300 import LIB_PATH
+    out = subprocess.run(["nm", "-D", "--defined-only", LIB_PATH], capture_output=True, text=True,
+                         check=True).stdout
+    exported = {ln.split()[-1] for ln in out.splitlines() if ln.strip()}
+    missing = [n for n in _declared_functions() if n not in exported]
+    assert not missing, missing
+    for n in _declared_functions():
+        assert hasattr(lib, n)
+
+
+def test_opts_defaults(lib):
+    import paper_2604_00567_b300 as dsfft
+    o = dsfft.PlanOpts()
+    assert lib.fft_plan_opts_init(1, ctypes.byref(o)) == 0
+    assert o.lf_eps == 1e-7 and o.scale_forward == 1 and o.scale_inverse == 0 and o.device == -1
+    assert lib.fft_plan_opts_init(0, ctypes.byref(o)) == 0
+    assert o.scale_forward == 0
+    assert lib.fft_plan_opts_init(7, ctypes.byref(o)) == 1
+    assert lib.fft_plan_opts_init(0, None) == 1
+
+
+def test_host_side_validation_without_gpu(lib):
+    """Errors detected before any CUDA call: bad sizes, enums, options, null
+    handles."""
+    import paper_2604_00567_b300 as dsfft
+    h = ctypes.c_void_p()
+    for n in (0, 1, 3, 6, 1000, 1 << 25, -4):
+        assert lib.fft_plan_create(ctypes.byref(h), n, 0, 2, None) == 2
+    assert lib.fft_plan_create(ctypes.byref(h), 1024, 9, 2, None) == 1
+    assert lib.fft_plan_create(ctypes.byref(h), 1024, 0, 9, None) == 1
+    assert lib.fft_plan_create(None, 1024, 0, 2, None) == 1
+    o = dsfft.PlanOpts()
+    lib.fft_plan_opts_init(0, ctypes.byref(o))
+    o.lf_eps = 0.0
+    assert lib.fft_plan_create(ctypes.byref(h), 1024, 0, 0, ctypes.byref(o)) == 1
+    lib.fft_plan_opts_init(0, ctypes.byref(o))
+    o.reserved[2] = 5
+    assert lib.fft_plan_create(ctypes.byref(h), 1024, 0, 2, ctypes.byref(o)) == 1
+    lib.fft_plan_opts_init(0, ctypes.byref(o))
+    o.scale_forward = 3
+    assert lib.fft_plan_create(ctypes.byref(h), 1024, 0, 2, ctypes.byref(o)) == 1
+    assert lib.fft_exec(None, None, None, 1, -1, None) == 1
+    assert lib.fft_plan_destroy(None) == 0
+    assert lib.fft_plan_get_info(None, None) == 1
+    assert lib.fft_plan_get_table(None, -1, None, 0) == 1
+    assert lib.fft_status_string(2).decode().startswith("invalid size")
+    assert lib.fft_status_string(99).decode() == "unknown status"
+
+
+def test_status_codes_match_binding():
+    import paper_2604_00567_b300 as dsfft
+    hdr = open(os.path.join(ROOT, "include", "dsfft.h")).read()
+    for code, name in dsfft.STATUS.items():
+        assert re.search(rf"\b{name}\s*=\s*{code}\b", hdr), name
