@@ -137,8 +137,9 @@ fft_status fft_exec(const fft_plan *plan, const void *in, void *out, int64_t bat
  *   FP32 : word0 = ratio t (float), word1 = multiplier m (float),
  *          word2 = sigma*m (float), word3 = path (0 cosine, 1 sine)
  *   FP16/BF16: word0 = (lo: -t, hi: t), word1 = (lo: sigma*m, hi: m),
- *          word2 = byte-permute selector of the operand swap,
- *          word3 = path (0 cosine, 1 sine)
+ *          word2 = byte-permute selector of the operand swap (0x1032 on
+ *          the cosine path, 0x3210 on the sine path),
+ *          word3 = (lo: -sigma*m, hi: -m)
  * where sigma = +1 on the cosine path and -1 on the sine path and m already
  * carries the x0.5 of a scaled direction.  Synchronous. */
 fft_status fft_plan_get_table(const fft_plan *plan, fft_direction dir, void *host_dst,

@@ -204,7 +204,10 @@ class Plan:
         """Decode the packed table: ``(t, m, path)`` as float64/float64/int32
         arrays (m includes the x0.5 of a scaled direction)."""
         raw = self.raw_table(direction)
-        path = raw[:, 3].astype(np.int32)
+        if self.precision == "fp32":
+            path = raw[:, 3].astype(np.int32)
+        else:
+            path = (raw[:, 2] == 0x3210).astype(np.int32)
         if self.precision == "fp32":
             t = raw[:, 0].view(np.float32).astype(np.float64)
             m = raw[:, 1].view(np.float32).astype(np.float64)

@@ -17,7 +17,8 @@ struct fft_plan {
   double eps;
   int scale[2];         // [0] forward, [1] inverse
   int device;
-  uint4 *table[2];      // packed tables, [0] forward, [1] inverse
+  uint4 *table[2];      // packed tables (N/2 entries), [0] forward, [1] inverse
+  uint4 *twp[2];        // per-pass copies (N - 1 entries) read by the kernels
   int kernel;           // 0 fused
   FusedShape shape;
   int cos_count, sin_count;
@@ -142,11 +143,15 @@ fft_status fft_plan_create(fft_plan **plan, int64_t n, fft_precision prec, fft_f
   do {
     if ((e = cudaMalloc(&p->table[0], entries * sizeof(uint4))) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc table"); break; }
     if ((e = cudaMalloc(&p->table[1], entries * sizeof(uint4))) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc table"); break; }
+    if ((e = cudaMalloc(&p->twp[0], (size_t)(n - 1) * sizeof(uint4))) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc table"); break; }
+    if ((e = cudaMalloc(&p->twp[1], (size_t)(n - 1) * sizeof(uint4))) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc table"); break; }
     if ((e = cudaMalloc(&counts, 2 * sizeof(int))) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc counts"); break; }
     if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) { status = cuda_fail(e, "stream"); break; }
     if ((e = cudaMemsetAsync(counts, 0, 2 * sizeof(int), st)) != cudaSuccess) { status = cuda_fail(e, "memset"); break; }
     if ((e = launch_build_table(log2n, fac, opts.lf_eps, prec, 0, p->scale[0], p->table[0], counts, st)) != cudaSuccess) { status = cuda_fail(e, "table build"); break; }
     if ((e = launch_build_table(log2n, fac, opts.lf_eps, prec, 1, p->scale[1], p->table[1], nullptr, st)) != cudaSuccess) { status = cuda_fail(e, "table build"); break; }
+    if ((e = launch_per_pass_table(log2n, p->table[0], p->twp[0], st)) != cudaSuccess) { status = cuda_fail(e, "per-pass table"); break; }
+    if ((e = launch_per_pass_table(log2n, p->table[1], p->twp[1], st)) != cudaSuccess) { status = cuda_fail(e, "per-pass table"); break; }
     if ((e = cudaMemcpyAsync(host_counts, counts, 2 * sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess) { status = cuda_fail(e, "copy counts"); break; }
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) { status = cuda_fail(e, "table build sync"); break; }
     if ((e = prepare_fused(prec, log2n)) != cudaSuccess) { status = cuda_fail(e, "kernel attributes"); break; }
@@ -154,8 +159,10 @@ fft_status fft_plan_create(fft_plan **plan, int64_t n, fft_precision prec, fft_f
   if (st) cudaStreamDestroy(st);
   if (counts) cudaFree(counts);
   if (status != FFT_OK) {
-    if (p->table[0]) cudaFree(p->table[0]);
-    if (p->table[1]) cudaFree(p->table[1]);
+    for (int d = 0; d < 2; ++d) {
+      if (p->table[d]) cudaFree(p->table[d]);
+      if (p->twp[d]) cudaFree(p->twp[d]);
+    }
     delete p;
     return status;
   }
@@ -168,8 +175,10 @@ fft_status fft_plan_create(fft_plan **plan, int64_t n, fft_precision prec, fft_f
 fft_status fft_plan_destroy(fft_plan *plan) {
   if (!plan) return FFT_OK;
   DeviceGuard guard(plan->device);
-  if (plan->table[0]) cudaFree(plan->table[0]);
-  if (plan->table[1]) cudaFree(plan->table[1]);
+  for (int d = 0; d < 2; ++d) {
+    if (plan->table[d]) cudaFree(plan->table[d]);
+    if (plan->twp[d]) cudaFree(plan->twp[d]);
+  }
   delete plan;
   return FFT_OK;
 }
@@ -186,7 +195,7 @@ fft_status fft_exec(const fft_plan *plan, const void *in, void *out, int64_t bat
   const int d = dir == FFT_FORWARD ? 0 : 1;
   DeviceGuard guard(plan->device);
   if (guard.err != cudaSuccess) return cuda_fail(guard.err, "select device");
-  cudaError_t e = launch_fused(plan->prec, plan->log2n, plan->scale[d] != 0, in, out, batch, plan->table[d],
+  cudaError_t e = launch_fused(plan->prec, plan->log2n, plan->scale[d] != 0, in, out, batch, plan->twp[d],
                                (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "fused kernel launch");
   return FFT_OK;
@@ -215,7 +224,7 @@ fft_status fft_plan_get_info(const fft_plan *plan, fft_plan_info *info) {
   info->points_per_thread = 1 << plan->shape.log2r;
   info->threads_per_transform = plan->shape.threads_per_transform;
   info->transforms_per_block = plan->shape.transforms_per_block;
-  info->table_bytes = (int64_t)2 * (plan->n / 2) * (int64_t)sizeof(uint4);
+  info->table_bytes = (int64_t)2 * (plan->n / 2 + plan->n - 1) * (int64_t)sizeof(uint4);
   info->element_bytes = (int64_t)elem_bytes(plan->prec);
   info->scale_forward = plan->scale[0];
   info->scale_inverse = plan->scale[1];

@@ -4,7 +4,8 @@
 // Packed twiddle entry (16 bytes, one per k in [0, N/2)):
 //   FP32     : x = t, y = m, z = sigma*m, w = path (0 cosine, 1 sine)
 //   FP16/BF16: x = (lo -t, hi t), y = (lo sigma*m, hi m), z = byte-permute
-//              selector that builds the operand swap, w = path
+//              selector that builds the operand swap, w = -y = (lo -sigma*m,
+//              hi -m)
 // sigma = +1 on the cosine path, -1 on the sine path.
 //
 // Unified butterfly (branch-free form of the two factorizations; the
@@ -27,6 +28,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "internal.h"
 
 namespace dsfft {
@@ -37,6 +40,16 @@ __host__ __device__ constexpr int bitrev(int v, int bits) {
   int r = 0;
   for (int i = 0; i < bits; ++i) r |= ((v >> i) & 1) << (bits - 1 - i);
   return r;
+}
+
+// Compile-time loop: f(std::integral_constant<int, I>) for I in [BEGIN, END).
+// Keeps every register-array index a constant however deep the nesting.
+template <int BEGIN, int END, class F>
+__device__ __forceinline__ void static_for(F &&f) {
+  if constexpr (BEGIN < END) {
+    f(std::integral_constant<int, BEGIN>{});
+    static_for<BEGIN + 1, END>(f);
+  }
 }
 
 // Storage type of one complex element.
@@ -91,7 +104,6 @@ __device__ __forceinline__ uint32_t b2_mul(uint32_t a, uint32_t b) {
   asm("mul.rn.bf16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
   return d;
 }
-__device__ __forceinline__ uint32_t neg2(uint32_t a) { return a ^ 0x80008000u; }
 
 template <int PREC, bool SCALED> struct BflyPacked {
   static __device__ __forceinline__ uint32_t fma2(uint32_t a, uint32_t b, uint32_t c) {
@@ -108,7 +120,7 @@ template <int PREC, bool SCALED> struct BflyPacked {
     uint32_t ah = a;
     if (SCALED) ah = mul2(a, PREC == kFP16 ? 0x38003800u : 0x3F003F00u);  // x 0.5
     a = fma2(e.y, uv, ah);
-    b = fma2(neg2(e.y), uv, ah);
+    b = fma2(e.w, uv, ah);
   }
 };
 

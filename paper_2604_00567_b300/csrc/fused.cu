@@ -15,10 +15,22 @@
 // Z_P[tid + p T] (p in [0, R), T = N/R threads), which is coalesced for the
 // first stage (from HBM) and bank-conflict-free for the others; the last
 // stage writes X[tid + p T] (coalesced).
+//
+// Twiddles come from the plan's per-pass table: pass p uses entries
+// twp[2^p - 1 + j] = table[j N/2^(p+1)], j in [0, 2^p) (exact copies of the
+// rounded entries), so the lanes of a warp, which hold consecutive j, read
+// consecutive 16-byte entries.
 #include "common.cuh"
 #include "internal.h"
 
 namespace dsfft {
+
+// Streaming (evict-first) loads and stores of signal data: every element is
+// touched once, so it should not displace the twiddle table in L1/L2.
+__device__ __forceinline__ float2 ldcs(const float2 *p) { return __ldcs(p); }
+__device__ __forceinline__ uint32_t ldcs(const uint32_t *p) { return __ldcs(reinterpret_cast<const unsigned int *>(p)); }
+__device__ __forceinline__ void stcs(float2 *p, float2 v) { __stcs(p, v); }
+__device__ __forceinline__ void stcs(uint32_t *p, uint32_t v) { __stcs(reinterpret_cast<unsigned int *>(p), v); }
 
 template <int PREC, int LOG2N, int LOG2R, bool SCALED>
 struct Fused {
@@ -29,8 +41,13 @@ struct Fused {
   static constexpr int TPC = T >= 256 ? 1 : 256 / T;     // transforms per block
   static constexpr int TPB = T * TPC;
   static constexpr int NSTAGES = (LOG2N + LOG2R - 1) / LOG2R;
-  static constexpr int PADN = N + (N >> 5);              // one pad element per 32
+  static constexpr int PADN = N + (N >> 5);              // one pad element per 32 (conflict-free
+                                                         // exchanges for R = 32 (4-byte) / R = 16 (8-byte))
   static constexpr int SMEM = NSTAGES > 1 ? TPC * PADN * (int)sizeof(E) : 0;
+  // Blocks per SM the register allocation must allow: two 512-thread blocks
+  // for the largest 4-byte transforms (64 registers per thread), otherwise
+  // whatever the compiler needs.
+  static constexpr int MINB = (TPB == 512 && sizeof(E) == 4) ? 2 : 1;
 
   static __device__ __forceinline__ int pad(int idx) { return idx + (idx >> 5); }
 
@@ -38,26 +55,25 @@ struct Fused {
   template <int P, int RHO>
   static __device__ __forceinline__ void compute(E (&v)[R], int tid, const uint4 *__restrict__ tw) {
     constexpr int C = R >> RHO;   // independent groups per thread
-#pragma unroll
-    for (int c = 0; c < C; ++c) {
+    static_for<0, C>([&](auto c_) {
+      constexpr int c = decltype(c_)::value;
       const int g = tid + c * T;
       const int j = g & ((1 << P) - 1);
-#pragma unroll
-      for (int i = 0; i < RHO; ++i) {
-        const int half = 1 << (RHO - 1 - i);
-#pragma unroll
-        for (int ql = 0; ql < (1 << i); ++ql) {
-          const int k = (j + (ql << P)) << (LOG2N - P - i - 1);
-          const uint4 e = __ldg(tw + k);
-          const int qtop = bitrev(ql, i) << (RHO - i);
-#pragma unroll
-          for (int qh = 0; qh < half; ++qh) {
-            const int q = qtop | qh;
+      static_for<0, RHO>([&](auto i_) {
+        constexpr int i = decltype(i_)::value;
+        constexpr int half = 1 << (RHO - 1 - i);
+        static_for<0, (1 << i)>([&](auto ql_) {
+          constexpr int ql = decltype(ql_)::value;
+          // pass P+i, j_full = j + ql 2^P
+          const uint4 e = __ldg(tw + ((1 << (P + i)) - 1) + j + (ql << P));
+          constexpr int qtop = bitrev(ql, i) << (RHO - i);
+          static_for<0, half>([&](auto qh_) {
+            constexpr int q = qtop | decltype(qh_)::value;
             Bfly<PREC, SCALED>::run(v[c + q * C], v[c + (q + half) * C], e);
-          }
-        }
-      }
-    }
+          });
+        });
+      });
+    });
   }
 
   template <int S>
@@ -67,27 +83,33 @@ struct Fused {
     constexpr int RHO = (LOG2N - P) < LOG2R ? (LOG2N - P) : LOG2R;
     constexpr int C = R >> RHO;
     if constexpr (S > 0) {
-#pragma unroll
-      for (int p = 0; p < R; ++p) v[p] = sm[pad(tid + p * T)];
+      static_for<0, R>([&](auto p_) {
+        constexpr int p = decltype(p_)::value;
+        v[p] = sm[pad(tid + p * T)];
+      });
     }
     compute<P, RHO>(v, tid, tw);
     if constexpr (P + RHO == LOG2N) {
       if (active) {
-#pragma unroll
-        for (int c = 0; c < C; ++c)
-#pragma unroll
-          for (int q = 0; q < (1 << RHO); ++q)
-            dst[tid + c * T + (bitrev(q, RHO) << P)] = v[c + q * C];
+        static_for<0, C>([&](auto c_) {
+          constexpr int c = decltype(c_)::value;
+          static_for<0, (1 << RHO)>([&](auto q_) {
+            constexpr int q = decltype(q_)::value;
+            stcs(dst + tid + c * T + (bitrev(q, RHO) << P), v[c + q * C]);
+          });
+        });
       }
     } else {
       if constexpr (S > 0) __syncthreads();   // previous exchange fully read
-#pragma unroll
-      for (int c = 0; c < C; ++c) {
+      static_for<0, C>([&](auto c_) {
+        constexpr int c = decltype(c_)::value;
         const int g = tid + c * T;
         const int base = ((g >> P) << (P + RHO)) + (g & ((1 << P) - 1));
-#pragma unroll
-        for (int q = 0; q < (1 << RHO); ++q) sm[pad(base + (bitrev(q, RHO) << P))] = v[c + q * C];
-      }
+        static_for<0, (1 << RHO)>([&](auto q_) {
+          constexpr int q = decltype(q_)::value;
+          sm[pad(base + (bitrev(q, RHO) << P))] = v[c + q * C];
+        });
+      });
       __syncthreads();
       stages<S + 1>(v, sm, tid, tw, dst, active);
     }
@@ -95,7 +117,7 @@ struct Fused {
 };
 
 template <int PREC, int LOG2N, int LOG2R, bool SCALED>
-__global__ void __launch_bounds__(Fused<PREC, LOG2N, LOG2R, SCALED>::TPB)
+__global__ void __launch_bounds__(Fused<PREC, LOG2N, LOG2R, SCALED>::TPB, Fused<PREC, LOG2N, LOG2R, SCALED>::MINB)
     fused_fft_kernel(const typename Elem<PREC>::T *in, typename Elem<PREC>::T *out, int64_t batch,
                      const uint4 *__restrict__ tw) {
   using K = Fused<PREC, LOG2N, LOG2R, SCALED>;
@@ -109,11 +131,12 @@ __global__ void __launch_bounds__(Fused<PREC, LOG2N, LOG2R, SCALED>::TPB)
   E v[K::R];
   const E *src = in + tr * K::N;
   if (active) {
-#pragma unroll
-    for (int p = 0; p < K::R; ++p) v[p] = src[tid + p * K::T];
+    static_for<0, K::R>([&](auto p_) {
+      constexpr int p = decltype(p_)::value;
+      v[p] = ldcs(src + tid + p * K::T);
+    });
   } else {
-#pragma unroll
-    for (int p = 0; p < K::R; ++p) v[p] = E{};
+    static_for<0, K::R>([&](auto p_) { v[decltype(p_)::value] = E{}; });
   }
   K::template stages<0>(v, sm, tid, tw, out + tr * K::N, active);
 }
@@ -121,9 +144,12 @@ __global__ void __launch_bounds__(Fused<PREC, LOG2N, LOG2R, SCALED>::TPB)
 // ---------------------------------------------------------------------------
 // dispatch
 
+// Points per thread: 32 four-byte (FP16/BF16) or 16 eight-byte (FP32)
+// elements, so a thread's register block is 32 registers and every exchange
+// is bank-conflict-free with the one-in-32 padding.
 constexpr int fused_log2r(int prec, int log2n) {
-  (void)prec;
-  return log2n < 4 ? log2n : 4;
+  const int r = prec == kFP32 ? 4 : 5;
+  return log2n < r ? log2n : r;
 }
 
 template <int PREC, int LOG2N, bool SCALED>

@@ -14,6 +14,7 @@ constexpr int kFusedMaxLog2N = 14;   // whole transform staged on chip
 
 cudaError_t launch_build_table(int log2n, int fac, double eps, int prec, int inverse, int scaled,
                                uint4 *out, int *counts, cudaStream_t stream);
+cudaError_t launch_per_pass_table(int log2n, const uint4 *table, uint4 *twp, cudaStream_t stream);
 cudaError_t launch_fp64_table(int log2n, int fac, double eps, double *t, double *m, int *path,
                               cudaStream_t stream);
 

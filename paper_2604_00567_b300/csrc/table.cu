@@ -80,10 +80,29 @@ __global__ void build_table_kernel(int log2n, int fac, double eps, int prec, int
     w.x = ((tb ^ 0x8000u) & 0xFFFFu) | (tb << 16);        // (lo -t, hi t)
     w.y = (smb & 0xFFFFu) | (mb << 16);                   // (lo sigma*m, hi m)
     w.z = e.sine ? 0x3210u : 0x1032u;                     // X = cosine ? swap(b) : b
-    w.w = (uint32_t)e.sine;
+    w.w = w.y ^ 0x80008000u;                              // (lo -sigma*m, hi -m)
   }
   out[k] = w;
   if (counts) atomicAdd(&counts[e.sine], 1);
+}
+
+// Per-pass copy of the packed table: pass p (half-span 2^p) uses entry
+// table[j N/2^(p+1)] for j in [0, 2^p); it is stored at twp[2^p - 1 + j].
+__global__ void per_pass_table_kernel(int log2n, const uint4 *__restrict__ table, uint4 *__restrict__ twp) {
+  const int64_t n = 1LL << log2n;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // i in [0, N-1)
+  if (i >= n - 1) return;
+  int p = 63 - __clzll(i + 1);            // 2^p - 1 <= i < 2^(p+1) - 1
+  const int64_t j = i - ((1LL << p) - 1);
+  twp[i] = table[j << (log2n - p - 1)];
+}
+
+cudaError_t launch_per_pass_table(int log2n, const uint4 *table, uint4 *twp, cudaStream_t stream) {
+  const int64_t cnt = (1LL << log2n) - 1;
+  const int threads = 256;
+  const unsigned blocks = (unsigned)((cnt + threads - 1) / threads);
+  per_pass_table_kernel<<<blocks, threads, 0, stream>>>(log2n, table, twp);
+  return cudaGetLastError();
 }
 
 __global__ void fp64_table_kernel(int log2n, int fac, double eps, double *t, double *m, int *path) {

@@ -85,6 +85,9 @@ def test_packed_words_consistent(dsfft):
     lo_t, hi_t = raw[:, 0] & 0xFFFF, raw[:, 0] >> 16
     assert np.all((lo_t ^ hi_t) == 0x8000)
     lo_m, hi_m = raw[:, 1] & 0xFFFF, raw[:, 1] >> 16
-    sine = raw[:, 3] == 1
+    sine = raw[:, 2] == 0x3210
+    assert np.all(sine | (raw[:, 2] == 0x1032))
     assert np.all(((lo_m ^ hi_m) == 0x8000) == sine)
-    assert np.all(np.where(sine, raw[:, 2] == 0x3210, raw[:, 2] == 0x1032))
+    assert np.all(raw[:, 3] == (raw[:, 1] ^ 0x80008000))
+    _, _, p = plan.table(-1)
+    assert np.array_equal(p, sine.astype(np.int32))
