@@ -19,6 +19,7 @@ struct fft_plan {
   int device;
   uint4 *table[2];      // packed tables (N/2 entries), [0] forward, [1] inverse
   uint4 *twp[2];        // per-pass copies (N - 1 entries) read by the kernels
+  Stage0Twiddles tw0[2];  // host copy of the first min(N, 32) - 1 per-pass entries
   int kernel;           // 0 fused
   FusedShape shape;
   int cos_count, sin_count;
@@ -152,6 +153,11 @@ fft_status fft_plan_create(fft_plan **plan, int64_t n, fft_precision prec, fft_f
     if ((e = launch_build_table(log2n, fac, opts.lf_eps, prec, 1, p->scale[1], p->table[1], nullptr, st)) != cudaSuccess) { status = cuda_fail(e, "table build"); break; }
     if ((e = launch_per_pass_table(log2n, p->table[0], p->twp[0], st)) != cudaSuccess) { status = cuda_fail(e, "per-pass table"); break; }
     if ((e = launch_per_pass_table(log2n, p->table[1], p->twp[1], st)) != cudaSuccess) { status = cuda_fail(e, "per-pass table"); break; }
+    for (int d = 0; d < 2; ++d) {
+      const size_t cnt = (size_t)((n < 32 ? n : 32) - 1);
+      if ((e = cudaMemcpyAsync(p->tw0[d].e, p->twp[d], cnt * sizeof(uint4), cudaMemcpyDeviceToHost, st)) != cudaSuccess) break;
+    }
+    if (e != cudaSuccess) { status = cuda_fail(e, "copy stage-0 twiddles"); break; }
     if ((e = cudaMemcpyAsync(host_counts, counts, 2 * sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess) { status = cuda_fail(e, "copy counts"); break; }
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) { status = cuda_fail(e, "table build sync"); break; }
     if ((e = prepare_fused(prec, log2n)) != cudaSuccess) { status = cuda_fail(e, "kernel attributes"); break; }
@@ -195,7 +201,7 @@ fft_status fft_exec(const fft_plan *plan, const void *in, void *out, int64_t bat
   const int d = dir == FFT_FORWARD ? 0 : 1;
   DeviceGuard guard(plan->device);
   if (guard.err != cudaSuccess) return cuda_fail(guard.err, "select device");
-  cudaError_t e = launch_fused(plan->prec, plan->log2n, plan->scale[d] != 0, in, out, batch, plan->twp[d],
+  cudaError_t e = launch_fused(plan->prec, plan->log2n, plan->scale[d] != 0, in, out, batch, plan->twp[d], plan->tw0[d],
                                (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "fused kernel launch");
   return FFT_OK;

@@ -44,16 +44,24 @@ struct Fused {
   static constexpr int PADN = N + (N >> 5);              // one pad element per 32 (conflict-free
                                                          // exchanges for R = 32 (4-byte) / R = 16 (8-byte))
   static constexpr int SMEM = NSTAGES > 1 ? TPC * PADN * (int)sizeof(E) : 0;
-  // Blocks per SM the register allocation must allow: two 512-thread blocks
-  // for the largest 4-byte transforms (64 registers per thread), otherwise
-  // whatever the compiler needs.
-  static constexpr int MINB = (TPB == 512 && sizeof(E) == 4) ? 2 : 1;
+  // Blocks per SM the register allocation must allow: 1024 threads' worth
+  // (at most 64 registers per thread), so at least half the SM's warps can
+  // be resident.
+  static constexpr int MINB = TPB >= 1024 ? 1 : 1024 / TPB;
 
   static __device__ __forceinline__ int pad(int idx) { return idx + (idx >> 5); }
 
+  // A transform's threads share one warp when T <= 32; then the exchange
+  // needs only a warp barrier.
+  static __device__ __forceinline__ void sync() {
+    if constexpr (T <= 32) __syncwarp();
+    else __syncthreads();
+  }
+
   // rho radix-2 passes starting at pass P on the registers of one thread.
   template <int P, int RHO>
-  static __device__ __forceinline__ void compute(E (&v)[R], int tid, const uint4 *__restrict__ tw) {
+  static __device__ __forceinline__ void compute(E (&v)[R], int tid, const uint4 *__restrict__ tw,
+                                                 const Stage0Twiddles &tw0) {
     constexpr int C = R >> RHO;   // independent groups per thread
     static_for<0, C>([&](auto c_) {
       constexpr int c = decltype(c_)::value;
@@ -64,8 +72,11 @@ struct Fused {
         constexpr int half = 1 << (RHO - 1 - i);
         static_for<0, (1 << i)>([&](auto ql_) {
           constexpr int ql = decltype(ql_)::value;
-          // pass P+i, j_full = j + ql 2^P
-          const uint4 e = __ldg(tw + ((1 << (P + i)) - 1) + j + (ql << P));
+          // pass P+i, j_full = j + ql 2^P; the first stage (j = 0) reads the
+          // constant bank
+          uint4 e;
+          if constexpr (P == 0) e = tw0.e[((1 << i) - 1) + ql];
+          else e = __ldg(tw + ((1 << (P + i)) - 1) + j + (ql << P));
           constexpr int qtop = bitrev(ql, i) << (RHO - i);
           static_for<0, half>([&](auto qh_) {
             constexpr int q = qtop | decltype(qh_)::value;
@@ -78,7 +89,7 @@ struct Fused {
 
   template <int S>
   static __device__ __forceinline__ void stages(E (&v)[R], E *sm, int tid, const uint4 *__restrict__ tw,
-                                                E *dst, bool active) {
+                                                const Stage0Twiddles &tw0, E *dst, bool active) {
     constexpr int P = S * LOG2R;
     constexpr int RHO = (LOG2N - P) < LOG2R ? (LOG2N - P) : LOG2R;
     constexpr int C = R >> RHO;
@@ -88,7 +99,7 @@ struct Fused {
         v[p] = sm[pad(tid + p * T)];
       });
     }
-    compute<P, RHO>(v, tid, tw);
+    compute<P, RHO>(v, tid, tw, tw0);
     if constexpr (P + RHO == LOG2N) {
       if (active) {
         static_for<0, C>([&](auto c_) {
@@ -100,7 +111,7 @@ struct Fused {
         });
       }
     } else {
-      if constexpr (S > 0) __syncthreads();   // previous exchange fully read
+      if constexpr (S > 0) sync();   // previous exchange fully read
       static_for<0, C>([&](auto c_) {
         constexpr int c = decltype(c_)::value;
         const int g = tid + c * T;
@@ -110,8 +121,8 @@ struct Fused {
           sm[pad(base + (bitrev(q, RHO) << P))] = v[c + q * C];
         });
       });
-      __syncthreads();
-      stages<S + 1>(v, sm, tid, tw, dst, active);
+      sync();
+      stages<S + 1>(v, sm, tid, tw, tw0, dst, active);
     }
   }
 };
@@ -119,7 +130,7 @@ struct Fused {
 template <int PREC, int LOG2N, int LOG2R, bool SCALED>
 __global__ void __launch_bounds__(Fused<PREC, LOG2N, LOG2R, SCALED>::TPB, Fused<PREC, LOG2N, LOG2R, SCALED>::MINB)
     fused_fft_kernel(const typename Elem<PREC>::T *in, typename Elem<PREC>::T *out, int64_t batch,
-                     const uint4 *__restrict__ tw) {
+                     const uint4 *__restrict__ tw, const __grid_constant__ Stage0Twiddles tw0) {
   using K = Fused<PREC, LOG2N, LOG2R, SCALED>;
   using E = typename K::E;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -138,7 +149,7 @@ __global__ void __launch_bounds__(Fused<PREC, LOG2N, LOG2R, SCALED>::TPB, Fused<
   } else {
     static_for<0, K::R>([&](auto p_) { v[decltype(p_)::value] = E{}; });
   }
-  K::template stages<0>(v, sm, tid, tw, out + tr * K::N, active);
+  K::template stages<0>(v, sm, tid, tw, tw0, out + tr * K::N, active);
 }
 
 // ---------------------------------------------------------------------------
@@ -153,14 +164,15 @@ constexpr int fused_log2r(int prec, int log2n) {
 }
 
 template <int PREC, int LOG2N, bool SCALED>
-static cudaError_t launch_one(const void *in, void *out, int64_t batch, const uint4 *tw, cudaStream_t stream) {
+static cudaError_t launch_one(const void *in, void *out, int64_t batch, const uint4 *tw, const Stage0Twiddles &tw0,
+                              cudaStream_t stream) {
   constexpr int LOG2R = fused_log2r(PREC, LOG2N);
   using K = Fused<PREC, LOG2N, LOG2R, SCALED>;
   using E = typename K::E;
   auto kern = fused_fft_kernel<PREC, LOG2N, LOG2R, SCALED>;
   const int64_t blocks = (batch + K::TPC - 1) / K::TPC;
   if (blocks > 0x7FFFFFFF) return cudaErrorInvalidConfiguration;
-  kern<<<(unsigned)blocks, K::TPB, K::SMEM, stream>>>(static_cast<const E *>(in), static_cast<E *>(out), batch, tw);
+  kern<<<(unsigned)blocks, K::TPB, K::SMEM, stream>>>(static_cast<const E *>(in), static_cast<E *>(out), batch, tw, tw0);
   return cudaGetLastError();
 }
 
@@ -170,12 +182,18 @@ template <int PREC, int LOG2N>
 static cudaError_t prepare_one() {
   constexpr int LOG2R = fused_log2r(PREC, LOG2N);
   using K = Fused<PREC, LOG2N, LOG2R, false>;
-  if (K::SMEM <= 48 * 1024) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(fused_fft_kernel<PREC, LOG2N, LOG2R, false>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(fused_fft_kernel<PREC, LOG2N, LOG2R, true>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM);
+  for (auto kern : {fused_fft_kernel<PREC, LOG2N, LOG2R, false>, fused_fft_kernel<PREC, LOG2N, LOG2R, true>}) {
+    // as much shared memory as the SM offers, so occupancy is not capped by
+    // the default L1/shared split
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    if (K::SMEM > 48 * 1024) {
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
 }
 
 template <int PREC, int LOG2N>
@@ -185,7 +203,8 @@ static FusedShape shape_one() {
   return FusedShape{LOG2R, K::T, K::TPC, K::TPB, K::SMEM};
 }
 
-using LaunchFn = cudaError_t (*)(const void *, void *, int64_t, const uint4 *, cudaStream_t);
+using LaunchFn = cudaError_t (*)(const void *, void *, int64_t, const uint4 *, const Stage0Twiddles &,
+                                 cudaStream_t);
 using ShapeFn = FusedShape (*)();
 using PrepareFn = cudaError_t (*)();
 
@@ -215,14 +234,14 @@ cudaError_t prepare_fused(int prec, int log2n) {
 }
 
 cudaError_t launch_fused(int prec, int log2n, bool scaled, const void *in, void *out, int64_t batch,
-                         const uint4 *table, cudaStream_t stream) {
+                         const uint4 *table, const Stage0Twiddles &tw0, cudaStream_t stream) {
   if (log2n < 1 || log2n > kFusedMaxLog2N) return cudaErrorInvalidValue;
   const int i = log2n - 1;
   LaunchFn f;
   if (prec == kFP32) f = scaled ? T32::scaled[i] : T32::plain[i];
   else if (prec == kFP16) f = scaled ? T16::scaled[i] : T16::plain[i];
   else f = scaled ? TB16::scaled[i] : TB16::plain[i];
-  return f(in, out, batch, table, stream);
+  return f(in, out, batch, table, tw0, stream);
 }
 
 }  // namespace dsfft

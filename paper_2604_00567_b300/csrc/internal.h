@@ -30,8 +30,16 @@ FusedShape fused_shape(int prec, int log2n);
 
 cudaError_t prepare_fused(int prec, int log2n);
 
-// Fused on-chip transform of `batch` signals of length 2^log2n.
+// Twiddles of the first register stage (passes 0 .. log2(R)-1, whose j is 0
+// for every thread): the first 2^r - 1 per-pass entries, passed by value so
+// the kernel reads them from the constant bank.
+struct Stage0Twiddles {
+  uint4 e[31];
+};
+
+// Fused on-chip transform of `batch` signals of length 2^log2n.  `twp` is
+// the device per-pass table, `tw0` its first entries.
 cudaError_t launch_fused(int prec, int log2n, bool scaled, const void *in, void *out, int64_t batch,
-                         const uint4 *table, cudaStream_t stream);
+                         const uint4 *twp, const Stage0Twiddles &tw0, cudaStream_t stream);
 
 }  // namespace dsfft
