@@ -182,11 +182,13 @@ template <int PREC, int LOG2N>
 static cudaError_t prepare_one() {
   constexpr int LOG2R = fused_log2r(PREC, LOG2N);
   using K = Fused<PREC, LOG2N, LOG2R, false>;
+  // Shared-memory carveout: enough for the blocks the register budget lets
+  // reside (MINB, at least one), the rest stays L1 for the twiddle table.
+  const int per_block = K::SMEM + 1024;
+  int carve = (int)((100LL * per_block * (K::MINB > 0 ? K::MINB : 1) + 228 * 1024 - 1) / (228 * 1024));
+  carve = carve < 1 ? 1 : carve > 100 ? 100 : carve;
   for (auto kern : {fused_fft_kernel<PREC, LOG2N, LOG2R, false>, fused_fft_kernel<PREC, LOG2N, LOG2R, true>}) {
-    // as much shared memory as the SM offers, so occupancy is not capped by
-    // the default L1/shared split
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                         cudaSharedmemCarveoutMaxShared);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, carve);
     if (e != cudaSuccess) return e;
     if (K::SMEM > 48 * 1024) {
       e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM);

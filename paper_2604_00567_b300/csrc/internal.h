@@ -42,4 +42,11 @@ struct Stage0Twiddles {
 cudaError_t launch_fused(int prec, int log2n, bool scaled, const void *in, void *out, int64_t batch,
                          const uint4 *twp, const Stage0Twiddles &tw0, cudaStream_t stream);
 
+// N > 2^14: two sweeps over HBM (passes [0, ceil(m/2)) then the rest).
+// `in` and `out` must differ; sweep 2 runs in place on `out`.
+void sweep_split(int log2n, int *ls1, int *ls2);
+cudaError_t prepare_sweeps(int prec, int log2n);
+cudaError_t launch_sweeps(int prec, int log2n, bool scaled, const void *in, void *out, int64_t batch,
+                          const uint4 *twp, cudaStream_t stream);
+
 }  // namespace dsfft

@@ -81,7 +81,10 @@ def signal(seed: int, batch: int, N: int, precision: str = "fp32", dist: str = "
     else:
         raise ValueError(f"unknown distribution {dist!r}")
     v = round_storage(v, precision)
-    return (v[0::2] + 1j * v[1::2]).reshape(batch, N)
+    out = np.empty(batch * N, dtype=np.complex128)
+    out.real = v[0::2]      # assigned, not computed: keeps the sign of zeros
+    out.imag = v[1::2]
+    return out.reshape(batch, N)
 
 
 def to_torch(x: np.ndarray, precision: str, device="cpu"):
@@ -107,7 +110,10 @@ def from_torch(t, precision: str) -> np.ndarray:
     if precision == "fp32":
         return t.numpy().astype(np.complex128)
     f = t.to(torch.float32).numpy().astype(np.float64)
-    return f[..., 0] + 1j * f[..., 1]
+    out = np.empty(f.shape[:-1], dtype=np.complex128)
+    out.real = f[..., 0]    # assigned, not computed: x + 1j*y turns -0 into +0
+    out.imag = f[..., 1]
+    return out
 
 
 def device_signal(batch: int, N: int, precision: str, seed: int, dist: str = "uniform",

@@ -1,0 +1,86 @@
+"""GPU parity of the two-sweep path (N > 2^14) against the CPU oracle: bit-
+exact against the op-by-op emulation, FP64 tolerances, and the largest size
+(N = 2^24) checked on sampled bins and by its round trip."""
+import numpy as np
+import pytest
+
+import oracle as orc
+from gpu_util import assert_bitexact, emulate, gpu_fft
+from paper_2604_00567_b300 import signals
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dsfft():
+    import paper_2604_00567_b300 as m
+    m.lib()
+    return m
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16", "bf16"])
+@pytest.mark.parametrize("log2n", [15, 16, 17])
+def test_sweeps_bitexact(dsfft, prec, log2n):
+    N = 1 << log2n
+    x = signals.signal(800 + log2n, 3, N, prec)
+    plan = dsfft.Plan(N, prec, "dual_select")
+    assert plan.info()["kernel"] == 1 and plan.info()["launches"] == 2
+    for d in (-1, 1):
+        assert_bitexact(gpu_fft(plan, x, d), emulate(plan, x, d), f"N=2^{log2n} {prec} dir={d}")
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+def test_sweeps_n2pow20_bitexact(dsfft, prec):
+    N = 1 << 20
+    x = signals.signal(820, 1, N, prec)
+    plan = dsfft.Plan(N, prec, "dual_select")
+    assert_bitexact(gpu_fft(plan, x), emulate(plan, x), f"N=2^20 {prec}")
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 2e-6), ("fp16", 4e-3)])
+@pytest.mark.parametrize("log2n", [16, 18, 20])
+def test_sweeps_accuracy_vs_fp64(dsfft, prec, tol, log2n):
+    N = 1 << log2n
+    x = signals.signal(830 + log2n, 2, N, prec)
+    plan = dsfft.Plan(N, prec, "dual_select")
+    ref = orc.fft_fp64(x) / (N if plan.scale_forward else 1)
+    assert orc.rel_l2(gpu_fft(plan, x), ref) < tol
+
+
+def test_n2pow24_sampled_bins_and_round_trip(dsfft):
+    """N = 2^24 complex64: sampled output bins against the FP64 DFT, and the
+    forward + inverse round trip (Section V, ~1e-7 in FP32)."""
+    import torch
+    N = 1 << 24
+    x = signals.signal(840, 1, N, "fp32")
+    plan = dsfft.Plan(N, "fp32", "dual_select")
+    xt = signals.to_torch(x, "fp32", "cuda")
+    y = plan.exec(xt)
+    z = plan.exec(y, direction=1)
+    torch.cuda.synchronize()
+    yh = y.cpu().numpy().astype(np.complex128)[0]
+    for k in (0, 1, 12345, N // 2, N - 1):
+        ref = orc.dft_bin(x[0], k)
+        assert abs(yh[k] - ref) < 2e-6 * np.sqrt(N)
+    err = orc.rel_l2(z.cpu().numpy().astype(np.complex128) / N, x)
+    assert err < 5e-7
+
+
+def test_sweeps_reject_in_place(dsfft):
+    import torch
+    plan = dsfft.Plan(1 << 15, "fp16", "dual_select")
+    x = torch.zeros((1, 1 << 15, 2), dtype=torch.float16, device="cuda")
+    with pytest.raises(dsfft.DsfftError) as e:
+        plan.exec(x, out=x)
+    assert e.value.status == 3
+
+
+def test_batch_of_eight_large(dsfft):
+    """Batch 8 at N = 2^20 (complex-FP16, config of the large-N study):
+    every transform equals the single-transform result."""
+    N = 1 << 20
+    x = signals.signal(850, 8, N, "fp16")
+    plan = dsfft.Plan(N, "fp16", "dual_select")
+    y = gpu_fft(plan, x)
+    for b in (0, 7):
+        assert_bitexact(y[b:b + 1], gpu_fft(plan, x[b:b + 1]), f"batch member {b}")
