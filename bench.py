@@ -373,6 +373,26 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_exec_only(args):
+    """Profiling driver: plan + seeded input for one N, `--iters` fft_exec
+    calls on a `--batch-mib` batch, nothing timed (for ncu captures)."""
+    import torch
+    import paper_2604_00567_b300 as dsfft
+    from paper_2604_00567_b300 import signals
+    l, prec = args.exec_only, args.precision
+    n = 1 << l
+    eb = 8 if prec == "fp32" else 4
+    batch = max(1, (args.batch_mib << 20) // (eb * n))
+    plan = dsfft.Plan(n, prec, args.factorization)
+    x = signals.device_signal(batch, n, prec, seed=l)
+    y = torch.empty_like(x)
+    for _ in range(args.iters):
+        plan.exec(x, out=y)
+    torch.cuda.synchronize()
+    print(json.dumps({"exec_only": True, "N": n, "precision": prec, "batch": batch, "iters": args.iters,
+                      "kernel": plan.info()["kernel"], "launches_per_exec": plan.info()["launches"]}))
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -381,7 +401,17 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--log2n", type=int, nargs="+", default=list(LOG2NS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--exec-only", type=int, metavar="LOG2N",
+                    help="profiling driver: run --iters transforms of one size and exit")
+    ap.add_argument("--precision", default="fp16", choices=["fp32", "fp16", "bf16"])
+    ap.add_argument("--factorization", default="dual_select",
+                    choices=["dual_select", "linzer_feig_clamped", "cosine"])
+    ap.add_argument("--batch-mib", type=int, default=256)
+    ap.add_argument("--iters", type=int, default=2)
     args = ap.parse_args()
+    if args.exec_only is not None:
+        run_exec_only(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
