@@ -91,7 +91,9 @@ typedef struct fft_plan_info {
     int32_t log2n;
     int32_t precision;          /* fft_precision */
     int32_t factorization;      /* fft_factorization */
-    int32_t kernel;             /* 0 = fused on-chip transform, 1 = HBM sweeps */
+    int32_t kernel;             /* 0 = fused on-chip transform (N <= 2^14),
+                                   1 = two HBM sweeps, 2 = one launch on a
+                                   thread-block cluster (DSMEM) */
     int32_t launches;           /* kernel launches per fft_exec */
     int32_t points_per_thread;  /* register block of the fused kernel */
     int32_t threads_per_transform;
@@ -126,9 +128,11 @@ fft_status fft_plan_destroy(fft_plan *plan);
 
 /* Transform `batch` signals (layout above) from `in` to `out`, asynchronously
  * on `stream` (a cudaStream_t; NULL = legacy default stream).  `in` is never
- * modified unless in == out.  in == out (in-place) is supported for
- * N <= 2^14; larger N requires distinct buffers (FFT_ERR_UNSUPPORTED
- * otherwise).  batch == 0 is a no-op.  Device pointers, element-aligned. */
+ * modified unless in == out.  in == out (in-place) is supported except by
+ * the HBM-sweep kernel (fft_plan_info.kernel == 1: FP16/BF16 N >= 2^18,
+ * FP32 N >= 2^17), which returns FFT_ERR_UNSUPPORTED for it; partially
+ * overlapping buffers are not allowed.  batch == 0 is a no-op.  Device
+ * pointers, element-aligned. */
 fft_status fft_exec(const fft_plan *plan, const void *in, void *out, int64_t batch,
                     fft_direction dir, void *stream);
 

@@ -129,7 +129,7 @@ fft_status fft_plan_create(fft_plan **plan, int64_t n, fft_precision prec, fft_f
   p->scale[0] = opts.scale_forward;
   p->scale[1] = opts.scale_inverse;
   p->device = device;
-  p->kernel = log2n <= kFusedMaxLog2N ? 0 : 1;
+  p->kernel = log2n <= kFusedMaxLog2N ? 0 : cluster_log2k(prec, log2n) >= 0 ? 2 : 1;
   p->shape = fused_shape(prec, log2n < kFusedMaxLog2N ? log2n : kFusedMaxLog2N);
 
   const size_t entries = (size_t)(n / 2);
@@ -156,7 +156,8 @@ fft_status fft_plan_create(fft_plan **plan, int64_t n, fft_precision prec, fft_f
     if (e != cudaSuccess) { status = cuda_fail(e, "copy stage-0 twiddles"); break; }
     if ((e = cudaMemcpyAsync(host_counts, counts, 2 * sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess) { status = cuda_fail(e, "copy counts"); break; }
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) { status = cuda_fail(e, "table build sync"); break; }
-    e = p->kernel == 0 ? prepare_fused(prec, log2n) : prepare_sweeps(prec, log2n);
+    e = p->kernel == 0 ? prepare_fused(prec, log2n) : p->kernel == 2 ? prepare_cluster(prec, log2n)
+                                                                      : prepare_sweeps(prec, log2n);
     if (e != cudaSuccess) { status = cuda_fail(e, "kernel attributes"); break; }
   } while (0);
   if (st) cudaStreamDestroy(st);
@@ -197,18 +198,23 @@ fft_status fft_exec(const fft_plan *plan, const void *in, void *out, int64_t bat
   if (((uintptr_t)in % eb) != 0 || ((uintptr_t)out % eb) != 0) return FFT_ERR_INVALID_ARG;
   const int d = dir == FFT_FORWARD ? 0 : 1;
   if (plan->kernel == 1 && in == out) {
-    snprintf(g_last_error, sizeof g_last_error, "in-place transforms need N <= 2^%d", kFusedMaxLog2N);
+    snprintf(g_last_error, sizeof g_last_error, "in-place transforms are not supported by the HBM-sweep path");
     return FFT_ERR_UNSUPPORTED;
   }
   DeviceGuard guard(plan->device);
   if (guard.err != cudaSuccess) return cuda_fail(guard.err, "select device");
   cudaError_t e;
+  const bool scaled = plan->scale[d] != 0;
   if (plan->kernel == 0)
-    e = launch_fused(plan->prec, plan->log2n, plan->scale[d] != 0, in, out, batch, plan->twp[d], plan->tw0[d],
-                     (cudaStream_t)stream);
+    e = launch_fused(plan->prec, plan->log2n, scaled, in, out, batch, plan->twp[d], plan->tw0[d], (cudaStream_t)stream);
+  else if (plan->kernel == 2)
+    e = launch_cluster(plan->prec, plan->log2n, scaled, in, out, batch, plan->twp[d], (cudaStream_t)stream);
   else
-    e = launch_sweeps(plan->prec, plan->log2n, plan->scale[d] != 0, in, out, batch, plan->twp[d], (cudaStream_t)stream);
-  if (e != cudaSuccess) return cuda_fail(e, plan->kernel == 0 ? "fused kernel launch" : "sweep kernel launch");
+    e = launch_sweeps(plan->prec, plan->log2n, scaled, in, out, batch, plan->twp[d], (cudaStream_t)stream);
+  if (e != cudaSuccess) {
+    static const char *what[3] = {"fused kernel launch", "sweep kernel launch", "cluster kernel launch"};
+    return cuda_fail(e, what[plan->kernel]);
+  }
   return FFT_OK;
 }
 
@@ -231,7 +237,7 @@ fft_status fft_plan_get_info(const fft_plan *plan, fft_plan_info *info) {
   info->precision = plan->prec;
   info->factorization = plan->fac;
   info->kernel = plan->kernel;
-  info->launches = plan->kernel == 0 ? 1 : 2;
+  info->launches = plan->kernel == 1 ? 2 : 1;
   info->points_per_thread = 1 << plan->shape.log2r;
   info->threads_per_transform = plan->shape.threads_per_transform;
   info->transforms_per_block = plan->shape.transforms_per_block;

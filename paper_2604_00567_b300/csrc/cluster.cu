@@ -1,0 +1,204 @@
+// cluster.cu — one-launch FFT for N = 2^15 .. 2^17 on a thread-block
+// cluster: the transform stays on chip across K = 2..8 SMs.
+//
+// The m passes are split as in the two-sweep path (passes [0, LS1), then
+// [LS1, m)), but the intermediate Stockham array Z_LS1 lives in the
+// cluster's distributed shared memory instead of HBM:
+//   phase 1: CTA `rank` runs passes [0, LS1) on groups g = rank GC1 + lg
+//            (values x[g + q M2], q in [0, M1)) and keeps Z_LS1[g M1 + o]
+//            in its own shared memory;
+//   cluster barrier;
+//   phase 2: CTA `rank` reads, for groups g' = rank GC2 + lg, the values
+//            Z_LS1[g' + q M1] (q in [0, M2)) from the shared memory of CTA
+//            q / GC1 (DSMEM loads), runs passes [LS1, m) and stores
+//            X[g' + o M1] to HBM.
+// A second cluster barrier separates the remote reads from the reuse of the
+// buffer for phase 2's own exchanges.  Every radix-2 butterfly of the
+// pass-by-pass algorithm is executed with its own operands and twiddle, so
+// the output is bit-identical to it; HBM sees one read and one write.
+//
+// Shared layout (both phases): value (o, lg) at o GC + (lg ^ (o mod 32)).
+// Lanes of a warp are consecutive groups, so the local exchanges and the
+// phase-2 remote reads (lanes with consecutive g' and equal q) are all
+// bank-conflict-free.
+#include <cooperative_groups.h>
+
+#include "group.cuh"
+#include "internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace dsfft {
+
+__device__ __forceinline__ float2 cl_ldcs(const float2 *p) { return __ldcs(p); }
+__device__ __forceinline__ uint32_t cl_ldcs(const uint32_t *p) { return __ldcs(reinterpret_cast<const unsigned int *>(p)); }
+__device__ __forceinline__ void cl_stcs(float2 *p, float2 v) { __stcs(p, v); }
+__device__ __forceinline__ void cl_stcs(uint32_t *p, uint32_t v) { __stcs(reinterpret_cast<unsigned int *>(p), v); }
+
+// Distributed shared memory: map a local shared address into CTA `rank`'s
+// window and load from it.  Volatile: the loads must stay between the two
+// cluster barriers.
+__device__ __forceinline__ uint32_t dsmem_map(uint32_t local_addr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local_addr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void dsmem_ld(uint32_t addr, uint32_t &v) {
+  asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+}
+__device__ __forceinline__ void dsmem_ld(uint32_t addr, float2 &v) {
+  asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr) : "memory");
+}
+
+template <int PREC, int LOG2N, int LOG2K, bool SCALED>
+struct Clus {
+  using E = typename Elem<PREC>::T;
+  static constexpr int N = 1 << LOG2N;
+  static constexpr int K = 1 << LOG2K;
+  static constexpr int LS1 = (LOG2N + 1) / 2;
+  static constexpr int LS2 = LOG2N / 2;
+  static constexpr int M1 = 1 << LS1;
+  static constexpr int M2 = 1 << LS2;
+  static constexpr int GC1 = M2 / K;     // phase-1 groups per CTA
+  static constexpr int GC2 = M1 / K;     // phase-2 groups per CTA
+  using P1 = GroupPasses<PREC, LS1, SCALED>;
+  using P2 = GroupPasses<PREC, LS2, SCALED>;
+  static constexpr int R = P1::R;
+  static constexpr int TPB = GC1 * P1::T;
+  static constexpr int LOCAL = N / K;
+  static constexpr int SMEM = LOCAL * (int)sizeof(E);
+  static_assert(GC2 * P2::T == TPB, "both phases use the same threads");
+  static_assert(GC1 >= 32 && GC2 >= 32, "a warp must span 32 groups");
+  static_assert(K <= 8, "portable cluster size");
+  static_assert(GC1 % P2::T == 0, "a thread's phase-2 reads never straddle two owners");
+};
+
+template <int PREC, int LOG2N, int LOG2K, bool SCALED>
+__global__ void __cluster_dims__(1 << LOG2K, 1, 1) __launch_bounds__(Clus<PREC, LOG2N, LOG2K, SCALED>::TPB, 2)
+    cluster_fft_kernel(const typename Elem<PREC>::T *in, typename Elem<PREC>::T *out, int64_t batch,
+                       const uint4 *__restrict__ twp) {
+  using K = Clus<PREC, LOG2N, LOG2K, SCALED>;
+  using E = typename K::E;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  E *sm = reinterpret_cast<E *>(smem_raw);
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int64_t tr = (int64_t)blockIdx.x / K::K;
+  // the grid is exactly batch * K blocks, so every cluster is active
+  (void)batch;
+
+  E v[K::R];
+  // ---- phase 1: passes [0, LS1) ----
+  {
+    const int lg = threadIdx.x % K::GC1;
+    const int tid = threadIdx.x / K::GC1;
+    const int64_t g = (int64_t)rank * K::GC1 + lg;
+    const E *src = in + tr * K::N + g;
+    static_for<0, K::R>([&](auto p_) {
+      constexpr int p = decltype(p_)::value;
+      v[p] = cl_ldcs(src + (int64_t)(tid + p * K::P1::T) * K::M2);
+    });
+    auto at = [&](int o) { return o * K::GC1 + (lg ^ (o & 31)); };
+    K::P1::template run<true>(
+        v, tid, 0, 0, twp, [&](int idx, E val) { sm[at(idx)] = val; }, [&](int idx) { return sm[at(idx)]; },
+        [] { __syncthreads(); }, [&](int o, E val) { sm[at(o)] = val; });
+  }
+  cluster.sync();   // Z_LS1 complete in every CTA of the cluster
+  // ---- phase 2: passes [LS1, m) ----
+  {
+    // opaque copy of the thread index: stops the compiler from sharing
+    // phase 1's address arithmetic (and keeping it live) when GC1 == GC2
+    unsigned tx;
+    asm volatile("mov.u32 %0, %%tid.x;" : "=r"(tx));
+    const int lg = tx % K::GC2;
+    const int tid = tx / K::GC2;
+    const int gp = rank * K::GC2 + lg;          // g' in [0, M1)
+    // Z_LS1[g' + q M1] is value (o = g', group q) of CTA q / GC1; with
+    // q = tid + p T2 and T2 | GC1 the owner and the group's base are
+    // compile-time for each p
+    const uint32_t local_base = (uint32_t)__cvta_generic_to_shared(sm);
+    uint32_t rbase[K::K];
+    static_for<0, K::K>([&](auto r_) { rbase[decltype(r_)::value] = dsmem_map(local_base, decltype(r_)::value); });
+    static_for<0, K::R>([&](auto p_) {
+      constexpr int p = decltype(p_)::value;
+      constexpr int owner = (p * K::P2::T) / K::GC1;
+      constexpr int gl0 = (p * K::P2::T) % K::GC1;
+      const int off = gp * K::GC1 + ((gl0 + tid) ^ (gp & 31));
+      dsmem_ld(rbase[owner] + off * (uint32_t)sizeof(E), v[p]);
+    });
+    cluster.sync();   // every remote read done before the buffer is reused
+    auto at = [&](int o) { return o * K::GC2 + (lg ^ (o & 31)); };
+    E *dst = out + tr * K::N + gp;
+    K::P2::template run<false>(
+        v, tid, gp, K::LS1, twp, [&](int idx, E val) { sm[at(idx)] = val; }, [&](int idx) { return sm[at(idx)]; },
+        [] { __syncthreads(); }, [&](int o, E val) { cl_stcs(dst + (int64_t)o * K::M1, val); });
+  }
+}
+
+// ---------------------------------------------------------------------------
+// dispatch: (prec, log2n) -> cluster size K; 0 when the size is not handled
+
+int cluster_log2k(int prec, int log2n) {
+  if (prec == kFP32) return log2n == 15 ? 2 : log2n == 16 ? 3 : -1;
+  return log2n == 15 ? 1 : log2n == 16 ? 2 : log2n == 17 ? 3 : -1;
+}
+
+template <int PREC, int LOG2N, int LOG2K, bool SCALED>
+static cudaError_t launch_cluster_one(const void *in, void *out, int64_t batch, const uint4 *twp,
+                                      cudaStream_t stream) {
+  using K = Clus<PREC, LOG2N, LOG2K, SCALED>;
+  using E = typename K::E;
+  const int64_t blocks = batch * K::K;
+  if (blocks > 0x7FFFFFFF) return cudaErrorInvalidConfiguration;
+  cluster_fft_kernel<PREC, LOG2N, LOG2K, SCALED><<<(unsigned)blocks, K::TPB, K::SMEM, stream>>>(
+      static_cast<const E *>(in), static_cast<E *>(out), batch, twp);
+  return cudaGetLastError();
+}
+
+template <int PREC, int LOG2N, int LOG2K>
+static cudaError_t prepare_cluster_one() {
+  using K = Clus<PREC, LOG2N, LOG2K, false>;
+  for (auto kern : {cluster_fft_kernel<PREC, LOG2N, LOG2K, false>, cluster_fft_kernel<PREC, LOG2N, LOG2K, true>}) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t prepare_cluster(int prec, int log2n) {
+  switch (prec * 100 + log2n) {
+    case kFP32 * 100 + 15: return prepare_cluster_one<kFP32, 15, 2>();
+    case kFP32 * 100 + 16: return prepare_cluster_one<kFP32, 16, 3>();
+    case kFP16 * 100 + 15: return prepare_cluster_one<kFP16, 15, 1>();
+    case kFP16 * 100 + 16: return prepare_cluster_one<kFP16, 16, 2>();
+    case kFP16 * 100 + 17: return prepare_cluster_one<kFP16, 17, 3>();
+    case kBF16 * 100 + 15: return prepare_cluster_one<kBF16, 15, 1>();
+    case kBF16 * 100 + 16: return prepare_cluster_one<kBF16, 16, 2>();
+    case kBF16 * 100 + 17: return prepare_cluster_one<kBF16, 17, 3>();
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_cluster(int prec, int log2n, bool scaled, const void *in, void *out, int64_t batch,
+                           const uint4 *twp, cudaStream_t stream) {
+#define DSFFT_CL(P, L, LK)                                                                   \
+  case P * 100 + L:                                                                          \
+    return scaled ? launch_cluster_one<P, L, LK, true>(in, out, batch, twp, stream)          \
+                  : launch_cluster_one<P, L, LK, false>(in, out, batch, twp, stream);
+  switch (prec * 100 + log2n) {
+    DSFFT_CL(kFP32, 15, 2)
+    DSFFT_CL(kFP32, 16, 3)
+    DSFFT_CL(kFP16, 15, 1)
+    DSFFT_CL(kFP16, 16, 2)
+    DSFFT_CL(kFP16, 17, 3)
+    DSFFT_CL(kBF16, 15, 1)
+    DSFFT_CL(kBF16, 16, 2)
+    DSFFT_CL(kBF16, 17, 3)
+  }
+#undef DSFFT_CL
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace dsfft

@@ -1,0 +1,99 @@
+// group.cuh — register-stage execution of LS consecutive radix-2 passes on
+// one "group" of 2^LS values, shared by the sweep and cluster kernels.
+//
+// Before global pass P0 the Stockham array is Z_P0; the LS passes starting
+// at P0 mix, for each group g, the values Z_P0[g + q S] (q in [0, 2^LS),
+// S = N / 2^LS).  Local pass i at local index j_loc is global pass P0 + i at
+// j = jg + j_loc 2^P0 (jg = g mod 2^P0), whose twiddle is per-pass entry
+// 2^(P0+i) - 1 + j.  A thread keeps R = 2^LOG2R values of its group in
+// registers and runs up to LOG2R passes between exchanges; thread `tid`
+// (of T = 2^LS / R per group) starts with local values tid + p T and ends
+// with local outputs o = tid + c T + bitrev(q) C T.
+#pragma once
+
+#include "common.cuh"
+
+namespace dsfft {
+
+template <int PREC, int LS, bool SCALED>
+struct GroupPasses {
+  using E = typename Elem<PREC>::T;
+  static constexpr int LOG2R = PREC == kFP32 ? 4 : 5;
+  static constexpr int R = 1 << LOG2R;
+  static constexpr int M = 1 << LS;
+  static constexpr int T = M / R;
+
+  template <int PL, int RHO>
+  static __device__ __forceinline__ void compute(E (&v)[R], int tid, int64_t jg, int P0,
+                                                 const uint4 *__restrict__ twp) {
+    constexpr int C = R >> RHO;
+    static_for<0, C>([&](auto c_) {
+      constexpr int c = decltype(c_)::value;
+      // keep each group's twiddle loads next to their use: hoisting all
+      // C (2^RHO - 1) 16-byte entries ahead would exhaust the registers
+      if constexpr (c > 0) asm volatile("" ::: "memory");
+      const int gl = tid + c * T;
+      const int64_t jloc = gl & ((1 << PL) - 1);
+      static_for<0, RHO>([&](auto i_) {
+        constexpr int i = decltype(i_)::value;
+        constexpr int half = 1 << (RHO - 1 - i);
+        const int p = P0 + PL + i;                         // global pass
+        const uint4 *tp = twp + ((1LL << p) - 1) + jg + (jloc << P0);
+        static_for<0, (1 << i)>([&](auto ql_) {
+          constexpr int ql = decltype(ql_)::value;
+          const uint4 e = __ldg(tp + ((int64_t)ql << (PL + P0)));
+          constexpr int qtop = bitrev(ql, i) << (RHO - i);
+          static_for<0, half>([&](auto qh_) {
+            constexpr int q = qtop | decltype(qh_)::value;
+            Bfly<PREC, SCALED>::run(v[c + q * C], v[c + (q + half) * C], e);
+          });
+        });
+      });
+    });
+  }
+
+  // Runs all LS passes.  xw(idx, value) / xr(idx) write / read local
+  // Stockham index idx of this group in the exchange buffer, sync() orders
+  // the block between them, out(o, value) receives local output o.  With
+  // SYNC_OUT the block synchronises before the outputs (when out() writes
+  // the exchange buffer).
+  template <bool SYNC_OUT = false, int S = 0, class XW, class XR, class SYNC, class OUT>
+  static __device__ __forceinline__ void run(E (&v)[R], int tid, int64_t jg, int P0, const uint4 *__restrict__ twp,
+                                             XW &&xw, XR &&xr, SYNC &&sync, OUT &&out) {
+    constexpr int PL = S * LOG2R;
+    constexpr int RHO = (LS - PL) < LOG2R ? (LS - PL) : LOG2R;
+    constexpr int C = R >> RHO;
+    if constexpr (S > 0) {
+      static_for<0, R>([&](auto p_) {
+        constexpr int p = decltype(p_)::value;
+        v[p] = xr(tid + p * T);
+      });
+    }
+    compute<PL, RHO>(v, tid, jg, P0, twp);
+    if constexpr (PL + RHO == LS) {
+      if constexpr (SYNC_OUT && S > 0) sync();
+      static_for<0, C>([&](auto c_) {
+        constexpr int c = decltype(c_)::value;
+        static_for<0, (1 << RHO)>([&](auto q_) {
+          constexpr int q = decltype(q_)::value;
+          out(tid + c * T + (bitrev(q, RHO) << PL), v[c + q * C]);
+        });
+      });
+    } else {
+      if constexpr (S > 0) sync();
+      static_for<0, C>([&](auto c_) {
+        constexpr int c = decltype(c_)::value;
+        const int gl = tid + c * T;
+        const int base = ((gl >> PL) << (PL + RHO)) + (gl & ((1 << PL) - 1));
+        static_for<0, (1 << RHO)>([&](auto q_) {
+          constexpr int q = decltype(q_)::value;
+          xw(base + (bitrev(q, RHO) << PL), v[c + q * C]);
+        });
+      });
+      sync();
+      run<SYNC_OUT, S + 1>(v, tid, jg, P0, twp, xw, xr, sync, out);
+    }
+  }
+};
+
+}  // namespace dsfft

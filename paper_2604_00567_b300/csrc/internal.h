@@ -49,4 +49,12 @@ cudaError_t prepare_sweeps(int prec, int log2n);
 cudaError_t launch_sweeps(int prec, int log2n, bool scaled, const void *in, void *out, int64_t batch,
                           const uint4 *twp, cudaStream_t stream);
 
+// 2^15 <= N <= 2^17 (FP16/BF16) or <= 2^16 (FP32): one launch on a cluster
+// of 2^cluster_log2k CTAs whose distributed shared memory holds the
+// transform between the two halves of the passes.  -1 = not handled.
+int cluster_log2k(int prec, int log2n);
+cudaError_t prepare_cluster(int prec, int log2n);
+cudaError_t launch_cluster(int prec, int log2n, bool scaled, const void *in, void *out, int64_t batch,
+                           const uint4 *twp, cudaStream_t stream);
+
 }  // namespace dsfft

@@ -18,15 +18,33 @@ def dsfft():
     return m
 
 
+def _expected_kernel(prec, log2n):
+    """Cluster (DSMEM) kernel for FP16/BF16 2^15..2^17 and FP32 2^15..2^16,
+    two HBM sweeps above."""
+    limit = 16 if prec == "fp32" else 17
+    return 2 if log2n <= limit else 1
+
+
 @pytest.mark.parametrize("prec", ["fp32", "fp16", "bf16"])
-@pytest.mark.parametrize("log2n", [15, 16, 17])
-def test_sweeps_bitexact(dsfft, prec, log2n):
+@pytest.mark.parametrize("log2n", [15, 16, 17, 18])
+def test_large_bitexact(dsfft, prec, log2n):
     N = 1 << log2n
     x = signals.signal(800 + log2n, 3, N, prec)
     plan = dsfft.Plan(N, prec, "dual_select")
-    assert plan.info()["kernel"] == 1 and plan.info()["launches"] == 2
+    info = plan.info()
+    assert info["kernel"] == _expected_kernel(prec, log2n)
+    assert info["launches"] == (2 if info["kernel"] == 1 else 1)
     for d in (-1, 1):
         assert_bitexact(gpu_fft(plan, x, d), emulate(plan, x, d), f"N=2^{log2n} {prec} dir={d}")
+
+
+@pytest.mark.parametrize("prec,log2n", [("fp16", 16), ("fp32", 15), ("bf16", 17)])
+def test_cluster_in_place(dsfft, prec, log2n):
+    N = 1 << log2n
+    x = signals.signal(860 + log2n, 5, N, prec)
+    plan = dsfft.Plan(N, prec, "dual_select")
+    assert plan.info()["kernel"] == 2
+    assert_bitexact(gpu_fft(plan, x, inplace=True), gpu_fft(plan, x), f"in-place N=2^{log2n} {prec}")
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp16"])
@@ -68,8 +86,9 @@ def test_n2pow24_sampled_bins_and_round_trip(dsfft):
 
 def test_sweeps_reject_in_place(dsfft):
     import torch
-    plan = dsfft.Plan(1 << 15, "fp16", "dual_select")
-    x = torch.zeros((1, 1 << 15, 2), dtype=torch.float16, device="cuda")
+    plan = dsfft.Plan(1 << 18, "fp16", "dual_select")
+    assert plan.info()["kernel"] == 1
+    x = torch.zeros((1, 1 << 18, 2), dtype=torch.float16, device="cuda")
     with pytest.raises(dsfft.DsfftError) as e:
         plan.exec(x, out=x)
     assert e.value.status == 3
