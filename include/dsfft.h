@@ -44,6 +44,13 @@
 extern "C" {
 #endif
 
+/* Exported entry points; everything else in the library is hidden. */
+#if defined(__GNUC__)
+#define DSFFT_API __attribute__((visibility("default")))
+#else
+#define DSFFT_API
+#endif
+
 typedef enum fft_status {
     FFT_OK = 0,
     FFT_ERR_INVALID_ARG = 1,   /* null pointer, bad enum, negative batch */
@@ -111,7 +118,7 @@ typedef struct fft_plan fft_plan;
 /* Fill `opts` with the defaults for `prec`: lf_eps = 1e-7, device = -1,
  * scale_forward = HALF_PER_PASS for FP16/BF16 and NONE for FP32,
  * scale_inverse = NONE. */
-fft_status fft_plan_opts_init(fft_precision prec, fft_plan_opts *opts);
+DSFFT_API fft_status fft_plan_opts_init(fft_precision prec, fft_plan_opts *opts);
 
 /* Create a plan for length-N transforms (N = 2^m, 2 <= N <= 2^24).  Builds
  * the FP64 twiddle table of Algorithm 1 (or of Eqs. 4-6 / 7-9) on the GPU
@@ -119,12 +126,12 @@ fft_status fft_plan_opts_init(fft_precision prec, fft_plan_opts *opts);
  * the packed tables for both directions resident on the device.  Blocks
  * until the tables are built.  `opts` may be NULL (defaults).
  * On success *plan owns the device memory; release with fft_plan_destroy. */
-fft_status fft_plan_create(fft_plan **plan, int64_t n, fft_precision prec,
+DSFFT_API fft_status fft_plan_create(fft_plan **plan, int64_t n, fft_precision prec,
                            fft_factorization fac, const fft_plan_opts *opts);
 
 /* Release a plan (NULL is accepted).  Work already queued that uses the plan
  * must have completed. */
-fft_status fft_plan_destroy(fft_plan *plan);
+DSFFT_API fft_status fft_plan_destroy(fft_plan *plan);
 
 /* Transform `batch` signals (layout above) from `in` to `out`, asynchronously
  * on `stream` (a cudaStream_t; NULL = legacy default stream).  `in` is never
@@ -133,7 +140,7 @@ fft_status fft_plan_destroy(fft_plan *plan);
  * FP32 N >= 2^17), which returns FFT_ERR_UNSUPPORTED for it; partially
  * overlapping buffers are not allowed.  batch == 0 is a no-op.  Device
  * pointers, element-aligned. */
-fft_status fft_exec(const fft_plan *plan, const void *in, void *out, int64_t batch,
+DSFFT_API fft_status fft_exec(const fft_plan *plan, const void *in, void *out, int64_t batch,
                     fft_direction dir, void *stream);
 
 /* Copy the plan's packed device table for `dir` to host memory
@@ -146,26 +153,26 @@ fft_status fft_exec(const fft_plan *plan, const void *in, void *out, int64_t bat
  *          word3 = (lo: -sigma*m, hi: -m)
  * where sigma = +1 on the cosine path and -1 on the sine path and m already
  * carries the x0.5 of a scaled direction.  Synchronous. */
-fft_status fft_plan_get_table(const fft_plan *plan, fft_direction dir, void *host_dst,
+DSFFT_API fft_status fft_plan_get_table(const fft_plan *plan, fft_direction dir, void *host_dst,
                               size_t bytes);
 
 /* Describe the plan (kernel choice, launch shape, table sizes). */
-fft_status fft_plan_get_info(const fft_plan *plan, fft_plan_info *info);
+DSFFT_API fft_status fft_plan_get_info(const fft_plan *plan, fft_plan_info *info);
 
 /* Run the FP64 stage of the table builder on the current device and return
  * the unrounded entries for k in [0, N/2): ratio t, multiplier m (forward
  * direction, no scaling) and path (0 cosine, 1 sine), into host arrays of
  * N/2 elements each.  Synchronous.  Used to check the GPU's FP64
  * trigonometry against a host evaluation. */
-fft_status fft_twiddle_fp64(int64_t n, fft_factorization fac, double lf_eps,
+DSFFT_API fft_status fft_twiddle_fp64(int64_t n, fft_factorization fac, double lf_eps,
                             double *host_t, double *host_m, int32_t *host_path);
 
 /* Static description of a status code. */
-const char *fft_status_string(fft_status status);
+DSFFT_API const char *fft_status_string(fft_status status);
 
 /* Text of the last CUDA error seen by a library call on this host thread
  * ("" if none). */
-const char *fft_last_error_string(void);
+DSFFT_API const char *fft_last_error_string(void);
 
 #ifdef __cplusplus
 }

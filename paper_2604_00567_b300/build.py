@@ -19,7 +19,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # Every arithmetic step of the transform is an explicit correctly rounded
 # intrinsic; -fmad=false and no fast-math keep the compiler from contracting
 # or flushing anything else.
-CFLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-fmad=false", "-ftz=false",
+CFLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
+                 "-fmad=false", "-ftz=false",
                  "-prec-div=true", "-prec-sqrt=true", "-I" + os.path.join(ROOT, "include")]
 
 

@@ -17,10 +17,11 @@
 // pass-by-pass algorithm is executed with its own operands and twiddle, so
 // the output is bit-identical to it; HBM sees one read and one write.
 //
-// Shared layout (both phases): value (o, lg) at o GC + (lg ^ (o mod 32)).
-// Lanes of a warp are consecutive groups, so the local exchanges and the
-// phase-2 remote reads (lanes with consecutive g' and equal q) are all
-// bank-conflict-free.
+// Shared layout (both phases): value o of local group lg at
+// lg M + (o ^ (lg mod 32)), M the group length.  Lanes of a warp are
+// consecutive groups: their local accesses (same o) fall in distinct banks,
+// and the phase-2 remote reads (same phase-1 group q, consecutive o = g')
+// cover one contiguous, aligned 32-element block of the owner's memory.
 #include <cooperative_groups.h>
 
 #include "group.cuh"
@@ -98,7 +99,7 @@ __global__ void __cluster_dims__(1 << LOG2K, 1, 1) __launch_bounds__(Clus<PREC, 
       constexpr int p = decltype(p_)::value;
       v[p] = cl_ldcs(src + (int64_t)(tid + p * K::P1::T) * K::M2);
     });
-    auto at = [&](int o) { return o * K::GC1 + (lg ^ (o & 31)); };
+    auto at = [&](int o) { return lg * K::M1 + (o ^ (lg & 31)); };
     K::P1::template run<true>(
         v, tid, 0, 0, twp, [&](int idx, E val) { sm[at(idx)] = val; }, [&](int idx) { return sm[at(idx)]; },
         [] { __syncthreads(); }, [&](int o, E val) { sm[at(o)] = val; });
@@ -113,9 +114,9 @@ __global__ void __cluster_dims__(1 << LOG2K, 1, 1) __launch_bounds__(Clus<PREC, 
     const int lg = tx % K::GC2;
     const int tid = tx / K::GC2;
     const int gp = rank * K::GC2 + lg;          // g' in [0, M1)
-    // Z_LS1[g' + q M1] is value (o = g', group q) of CTA q / GC1; with
-    // q = tid + p T2 and T2 | GC1 the owner and the group's base are
-    // compile-time for each p
+    // Z_LS1[g' + q M1] is value o = g' of phase-1 group q, held by CTA
+    // q / GC1 at local group q mod GC1; with q = tid + p T2 and T2 | GC1 the
+    // owner and the group's base are compile-time for each p
     const uint32_t local_base = (uint32_t)__cvta_generic_to_shared(sm);
     uint32_t rbase[K::K];
     static_for<0, K::K>([&](auto r_) { rbase[decltype(r_)::value] = dsmem_map(local_base, decltype(r_)::value); });
@@ -123,11 +124,12 @@ __global__ void __cluster_dims__(1 << LOG2K, 1, 1) __launch_bounds__(Clus<PREC, 
       constexpr int p = decltype(p_)::value;
       constexpr int owner = (p * K::P2::T) / K::GC1;
       constexpr int gl0 = (p * K::P2::T) % K::GC1;
-      const int off = gp * K::GC1 + ((gl0 + tid) ^ (gp & 31));
+      const int gl = gl0 + tid;
+      const int off = gl * K::M1 + (gp ^ (gl & 31));
       dsmem_ld(rbase[owner] + off * (uint32_t)sizeof(E), v[p]);
     });
     cluster.sync();   // every remote read done before the buffer is reused
-    auto at = [&](int o) { return o * K::GC2 + (lg ^ (o & 31)); };
+    auto at = [&](int o) { return lg * K::M2 + (o ^ (lg & 31)); };
     E *dst = out + tr * K::N + gp;
     K::P2::template run<false>(
         v, tid, gp, K::LS1, twp, [&](int idx, E val) { sm[at(idx)] = val; }, [&](int idx) { return sm[at(idx)]; },

@@ -51,12 +51,20 @@ struct Fused {
 
   static __device__ __forceinline__ int pad(int idx) { return idx + (idx >> 5); }
 
-  // A transform's threads share one warp when T <= 32; then the exchange
-  // needs only a warp barrier.
-  static __device__ __forceinline__ void sync() {
-    if constexpr (T <= 32) __syncwarp();
-    else __syncthreads();
+  // Exchange barrier of one transform's T threads: a warp barrier when they
+  // share a warp, a named barrier per transform when a block holds several
+  // multi-warp transforms (so transforms do not wait for each other), else
+  // the block barrier.
+  static __device__ __forceinline__ void sync(int lt) {
+    if constexpr (T <= 32) {
+      __syncwarp();
+    } else if constexpr (TPC > 1) {
+      asm volatile("bar.sync %0, %1;" ::"r"(1 + lt), "r"(T) : "memory");
+    } else {
+      __syncthreads();
+    }
   }
+  static_assert(TPC <= 15 || T <= 32, "named barriers 1..15");
 
   // rho radix-2 passes starting at pass P on the registers of one thread.
   template <int P, int RHO>
@@ -88,15 +96,19 @@ struct Fused {
   }
 
   template <int S>
-  static __device__ __forceinline__ void stages(E (&v)[R], E *sm, int tid, const uint4 *__restrict__ tw,
+  static __device__ __forceinline__ void stages(E (&v)[R], E *sm, int tid, int lt, const uint4 *__restrict__ tw,
                                                 const Stage0Twiddles &tw0, E *dst, bool active) {
     constexpr int P = S * LOG2R;
     constexpr int RHO = (LOG2N - P) < LOG2R ? (LOG2N - P) : LOG2R;
     constexpr int C = R >> RHO;
     if constexpr (S > 0) {
+      // pad(tid + p T) = pad(tid) + p T + p T / 32 when 32 | T: one base
+      // address plus compile-time offsets
+      const int pt = pad(tid);
       static_for<0, R>([&](auto p_) {
         constexpr int p = decltype(p_)::value;
-        v[p] = sm[pad(tid + p * T)];
+        if constexpr (T % 32 == 0) v[p] = sm[pt + p * T + ((p * T) >> 5)];
+        else v[p] = sm[pad(tid + p * T)];
       });
     }
     compute<P, RHO>(v, tid, tw, tw0);
@@ -111,18 +123,24 @@ struct Fused {
         });
       }
     } else {
-      if constexpr (S > 0) sync();   // previous exchange fully read
+      if constexpr (S > 0) sync(lt);   // previous exchange fully read
+      // pad(base + off) = pad(base) + off + off / 32 when off is a multiple
+      // of 32 (P >= 5) or base is and off < 32 (P = 0, RHO = 5)
+      constexpr bool FOLD = P >= 5 || (P == 0 && RHO == 5);
       static_for<0, C>([&](auto c_) {
         constexpr int c = decltype(c_)::value;
         const int g = tid + c * T;
         const int base = ((g >> P) << (P + RHO)) + (g & ((1 << P) - 1));
+        const int pb = pad(base);
         static_for<0, (1 << RHO)>([&](auto q_) {
           constexpr int q = decltype(q_)::value;
-          sm[pad(base + (bitrev(q, RHO) << P))] = v[c + q * C];
+          constexpr int off = bitrev(q, RHO) << P;
+          if constexpr (FOLD) sm[pb + off + (off >> 5)] = v[c + q * C];
+          else sm[pad(base + off)] = v[c + q * C];
         });
       });
-      sync();
-      stages<S + 1>(v, sm, tid, tw, tw0, dst, active);
+      sync(lt);
+      stages<S + 1>(v, sm, tid, lt, tw, tw0, dst, active);
     }
   }
 };
@@ -149,7 +167,7 @@ __global__ void __launch_bounds__(Fused<PREC, LOG2N, LOG2R, SCALED>::TPB, Fused<
   } else {
     static_for<0, K::R>([&](auto p_) { v[decltype(p_)::value] = E{}; });
   }
-  K::template stages<0>(v, sm, tid, tw, tw0, out + tr * K::N, active);
+  K::template stages<0>(v, sm, tid, lt, tw, tw0, out + tr * K::N, active);
 }
 
 // ---------------------------------------------------------------------------
