@@ -167,6 +167,64 @@ DSFFT_API fft_status fft_plan_get_info(const fft_plan *plan, fft_plan_info *info
 DSFFT_API fft_status fft_twiddle_fp64(int64_t n, fft_factorization fac, double lf_eps,
                             double *host_t, double *host_m, int32_t *host_path);
 
+/* ------------------------------------------------------------------------ */
+/* Mixed batches: transforms of different sizes, precisions, factorizations
+ * and directions, each with its own input and output buffer, run as one
+ * persistent kernel launch (every transform with N <= 2^14) plus one launch
+ * per (size, precision, factorization, direction) group of larger transforms
+ * (cluster or sweep kernels reading the same per-transform pointers).  The
+ * persistent kernel takes tiles of equal-size transforms, largest first,
+ * from a device work counter.  Each transform's result is bit-identical to
+ * fft_exec of the same plan on that transform alone. */
+
+typedef struct fft_batch_item {
+    int64_t n;                /* transform length, as for fft_plan_create */
+    int32_t precision;        /* fft_precision */
+    int32_t factorization;    /* fft_factorization */
+    int32_t direction;        /* fft_direction */
+    int32_t reserved;         /* must be zero */
+    const void *in;           /* device pointer, element-aligned */
+    void *out;                /* device pointer; may equal `in` except for
+                                 sizes that use HBM sweeps */
+} fft_batch_item;
+
+typedef struct fft_batch fft_batch;
+
+typedef struct fft_batch_info {
+    int64_t items;             /* transforms in the batch */
+    int32_t plans;             /* distinct plans the batch created */
+    int32_t tiles;             /* work tiles of the persistent kernel */
+    int32_t persistent_blocks; /* blocks of the persistent launch */
+    int32_t large_groups;      /* groups of N > 2^14 launched separately */
+    int32_t launches;          /* kernel launches per fft_batch_exec */
+    int32_t graph_ready;       /* 1 once fft_batch_exec_graph captured */
+    int64_t device_bytes;      /* device memory the batch owns (tables,
+                                  descriptors, work counter) */
+} fft_batch_info;
+
+/* Build a batch from `count` items (copied; the buffers they point to are
+ * the caller's and must stay valid while the batch is used).  Plans are
+ * created once per distinct (n, precision, factorization); `opts` applies to
+ * every plan (NULL = the defaults of each item's precision).  Uploads the
+ * work descriptors; blocks until done. */
+DSFFT_API fft_status fft_batch_create(fft_batch **batch, const fft_batch_item *items, int64_t count,
+                                      const fft_plan_opts *opts);
+
+/* Run every transform of the batch asynchronously on `stream`. */
+DSFFT_API fft_status fft_batch_exec(fft_batch *batch, void *stream);
+
+/* Same work as fft_batch_exec, through a CUDA graph: the first call captures
+ * the launches (on a stream the batch owns) and instantiates the graph,
+ * every call launches the graph on `stream`.  Not thread-safe with itself on
+ * the same batch. */
+DSFFT_API fft_status fft_batch_exec_graph(fft_batch *batch, void *stream);
+
+DSFFT_API fft_status fft_batch_get_info(const fft_batch *batch, fft_batch_info *info);
+
+/* Release the batch, its plans and its graph (NULL accepted); queued work
+ * using it must have completed. */
+DSFFT_API fft_status fft_batch_destroy(fft_batch *batch);
+
 /* Static description of a status code. */
 DSFFT_API const char *fft_status_string(fft_status status);
 

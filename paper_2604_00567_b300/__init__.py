@@ -22,7 +22,7 @@ import threading
 
 import numpy as np
 
-__all__ = ["Plan", "lib", "twiddle_fp64", "DsfftError", "PRECISIONS", "FACTORIZATIONS",
+__all__ = ["Plan", "Batch", "lib", "twiddle_fp64", "DsfftError", "PRECISIONS", "FACTORIZATIONS",
            "FORWARD", "INVERSE"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -57,6 +57,19 @@ class PlanInfo(ctypes.Structure):
                 ("cos_count", ctypes.c_int32), ("sin_count", ctypes.c_int32)]
 
 
+class BatchItemC(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("precision", ctypes.c_int32), ("factorization", ctypes.c_int32),
+                ("direction", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("in_", ctypes.c_void_p), ("out", ctypes.c_void_p)]
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("items", ctypes.c_int64), ("plans", ctypes.c_int32), ("tiles", ctypes.c_int32),
+                ("persistent_blocks", ctypes.c_int32), ("large_groups", ctypes.c_int32),
+                ("launches", ctypes.c_int32), ("graph_ready", ctypes.c_int32),
+                ("device_bytes", ctypes.c_int64)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -82,8 +95,15 @@ def lib():
             L.fft_status_string.argtypes = [i32]
             L.fft_last_error_string.restype = ctypes.c_char_p
             L.fft_last_error_string.argtypes = []
+            L.fft_batch_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(BatchItemC), i64,
+                                           ctypes.POINTER(PlanOpts)]
+            L.fft_batch_exec.argtypes = [P, P]
+            L.fft_batch_exec_graph.argtypes = [P, P]
+            L.fft_batch_get_info.argtypes = [P, ctypes.POINTER(BatchInfo)]
+            L.fft_batch_destroy.argtypes = [P]
             for name in ("fft_plan_opts_init", "fft_plan_create", "fft_plan_destroy", "fft_exec",
-                         "fft_plan_get_table", "fft_plan_get_info", "fft_twiddle_fp64"):
+                         "fft_plan_get_table", "fft_plan_get_info", "fft_twiddle_fp64", "fft_batch_create",
+                         "fft_batch_exec", "fft_batch_exec_graph", "fft_batch_get_info", "fft_batch_destroy"):
                 getattr(L, name).restype = i32
             _lib = L
     return _lib
@@ -221,6 +241,64 @@ class Plan:
                 t = (thi.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
                 m = (mhi.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
         return t, m, path
+
+
+class Batch:
+    """A mixed batch: transforms of different sizes, precisions,
+    factorizations and directions, each with its own tensors, run as one
+    persistent launch (plus one launch per group of sizes above 2^14).
+
+    ``items``: iterable of ``(n, precision, factorization, direction, x, out)``
+    with ``x``/``out`` CUDA tensors in the layouts of :class:`Plan`."""
+
+    def __init__(self, items, lf_eps: float | None = None):
+        L = lib()
+        items = list(items)
+        arr = (BatchItemC * max(1, len(items)))()
+        self._keep = []
+        for i, (n, prec, fac, direction, x, out) in enumerate(items):
+            for t in (x, out):
+                if not t.is_cuda or not t.is_contiguous():
+                    raise ValueError("batch tensors must be contiguous CUDA tensors")
+            arr[i].n = int(n)
+            arr[i].precision = PRECISIONS[prec]
+            arr[i].factorization = FACTORIZATIONS[fac]
+            arr[i].direction = int(direction)
+            arr[i].reserved = 0
+            arr[i].in_ = x.data_ptr()
+            arr[i].out = out.data_ptr()
+            self._keep.append((x, out))
+        opts_p = None
+        if lf_eps is not None:
+            o = PlanOpts()
+            L.fft_plan_opts_init(0, ctypes.byref(o))
+            o.lf_eps = float(lf_eps)
+            opts_p = ctypes.byref(o)
+        h = ctypes.c_void_p()
+        _check(L.fft_batch_create(ctypes.byref(h), arr, len(items), opts_p), "fft_batch_create")
+        self._h = h
+
+    def exec(self, stream=None):
+        _check(lib().fft_batch_exec(self._h, _stream_handle(stream)), "fft_batch_exec")
+
+    def exec_graph(self, stream=None):
+        _check(lib().fft_batch_exec_graph(self._h, _stream_handle(stream)), "fft_batch_exec_graph")
+
+    def info(self) -> dict:
+        inf = BatchInfo()
+        _check(lib().fft_batch_get_info(self._h, ctypes.byref(inf)), "fft_batch_get_info")
+        return {k: getattr(inf, k) for k, _ in BatchInfo._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().fft_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def twiddle_fp64(n: int, factorization: str = "dual_select", lf_eps: float = 1e-7):

@@ -4,6 +4,11 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
+#include <map>
+#include <tuple>
+#include <vector>
+
 #include "../../include/dsfft.h"
 #include "internal.h"
 
@@ -67,6 +72,65 @@ size_t elem_bytes(int prec) { return prec == kFP32 ? 8 : 4; }
 }  // namespace
 
 extern "C" {
+
+struct fft_batch {
+  int device = 0;
+  std::vector<fft_plan *> plans;
+  int64_t count = 0;
+  BatchItem *d_items = nullptr;     // items reordered by group
+  BatchTile *d_tiles = nullptr;
+  unsigned *d_counter = nullptr;
+  int ntiles = 0;
+  int grid = 0;
+  struct Large {
+    const fft_plan *plan;
+    int dir;                        // 0 forward, 1 inverse
+    int64_t first, count;           // slice of d_items
+  };
+  std::vector<Large> large;
+  cudaStream_t capture_stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  int64_t device_bytes = 0;
+};
+
+namespace {
+
+// Queue every launch of the batch on `stream`.
+cudaError_t batch_enqueue(const fft_batch *b, cudaStream_t stream) {
+  cudaError_t e = cudaSuccess;
+  if (b->ntiles > 0) {
+    e = launch_batch_kernel(b->d_tiles, b->ntiles, b->d_items, b->d_counter, b->grid, stream);
+    if (e != cudaSuccess) return e;
+  }
+  for (const auto &g : b->large) {
+    const fft_plan *p = g.plan;
+    const bool scaled = p->scale[g.dir] != 0;
+    if (p->kernel == 2)
+      e = launch_cluster(p->prec, p->log2n, scaled, nullptr, nullptr, b->d_items + g.first, g.count, p->twp[g.dir],
+                         stream);
+    else
+      e = launch_sweeps(p->prec, p->log2n, scaled, nullptr, nullptr, b->d_items + g.first, g.count, p->twp[g.dir],
+                        stream);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+void batch_release(fft_batch *b) {
+  if (!b) return;
+  DeviceGuard guard(b->device);
+  if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+  if (b->d_items) cudaFree(b->d_items);
+  if (b->d_tiles) cudaFree(b->d_tiles);
+  if (b->d_counter) cudaFree(b->d_counter);
+  for (fft_plan *p : b->plans) fft_plan_destroy(p);
+  delete b;
+}
+
+}  // namespace
 
 const char *fft_status_string(fft_status s) {
   switch (s) {
@@ -208,9 +272,9 @@ fft_status fft_exec(const fft_plan *plan, const void *in, void *out, int64_t bat
   if (plan->kernel == 0)
     e = launch_fused(plan->prec, plan->log2n, scaled, in, out, batch, plan->twp[d], plan->tw0[d], (cudaStream_t)stream);
   else if (plan->kernel == 2)
-    e = launch_cluster(plan->prec, plan->log2n, scaled, in, out, batch, plan->twp[d], (cudaStream_t)stream);
+    e = launch_cluster(plan->prec, plan->log2n, scaled, in, out, nullptr, batch, plan->twp[d], (cudaStream_t)stream);
   else
-    e = launch_sweeps(plan->prec, plan->log2n, scaled, in, out, batch, plan->twp[d], (cudaStream_t)stream);
+    e = launch_sweeps(plan->prec, plan->log2n, scaled, in, out, nullptr, batch, plan->twp[d], (cudaStream_t)stream);
   if (e != cudaSuccess) {
     static const char *what[3] = {"fused kernel launch", "sweep kernel launch", "cluster kernel launch"};
     return cuda_fail(e, what[plan->kernel]);
@@ -276,6 +340,179 @@ fft_status fft_twiddle_fp64(int64_t n, fft_factorization fac, double lf_eps, dou
   if (m) cudaFree(m);
   if (path) cudaFree(path);
   return status;
+}
+
+fft_status fft_batch_create(fft_batch **batch, const fft_batch_item *items, int64_t count,
+                            const fft_plan_opts *opts) {
+  if (!batch) return FFT_ERR_INVALID_ARG;
+  *batch = nullptr;
+  if (count < 0 || (count > 0 && !items)) return FFT_ERR_INVALID_ARG;
+  if (count > 0x7FFFFFFFLL) return FFT_ERR_INVALID_SIZE;
+  // validate every item before touching the device
+  for (int64_t i = 0; i < count; ++i) {
+    const fft_batch_item &it = items[i];
+    if (it.precision < FFT_PREC_FP32 || it.precision > FFT_PREC_BF16) return FFT_ERR_INVALID_ARG;
+    if (it.factorization < FFT_FAC_LINZER_FEIG_CLAMPED || it.factorization > FFT_FAC_DUAL_SELECT)
+      return FFT_ERR_INVALID_ARG;
+    if (it.direction != FFT_FORWARD && it.direction != FFT_INVERSE) return FFT_ERR_INVALID_ARG;
+    if (it.reserved != 0 || !it.in || !it.out) return FFT_ERR_INVALID_ARG;
+    const size_t eb = elem_bytes(it.precision);
+    if (((uintptr_t)it.in % eb) != 0 || ((uintptr_t)it.out % eb) != 0) return FFT_ERR_INVALID_ARG;
+    const int l = ilog2_exact(it.n);
+    if (l < 1 || l > kMaxLog2N) return FFT_ERR_INVALID_SIZE;
+  }
+  fft_batch *b = new fft_batch();
+  b->count = count;
+  fft_status status = FFT_OK;
+  cudaError_t e = cudaGetDevice(&b->device);
+  if (e != cudaSuccess) {
+    delete b;
+    return cuda_fail(e, "cudaGetDevice");
+  }
+  // one plan per (n, precision, factorization)
+  std::map<std::tuple<int64_t, int, int>, fft_plan *> plan_of;
+  struct Ref {
+    fft_plan *plan;
+    int dir;
+    int64_t index;
+  };
+  std::vector<Ref> refs;
+  refs.reserve((size_t)count);
+  for (int64_t i = 0; i < count && status == FFT_OK; ++i) {
+    const fft_batch_item &it = items[i];
+    auto key = std::make_tuple(it.n, (int)it.precision, (int)it.factorization);
+    auto f = plan_of.find(key);
+    fft_plan *p = nullptr;
+    if (f == plan_of.end()) {
+      fft_plan_opts o;
+      fft_plan_opts_init((fft_precision)it.precision, &o);
+      if (opts) o = *opts;
+      status = fft_plan_create(&p, it.n, (fft_precision)it.precision, (fft_factorization)it.factorization, &o);
+      if (status != FFT_OK) break;
+      plan_of[key] = p;
+      b->plans.push_back(p);
+    } else {
+      p = f->second;
+    }
+    if (p->kernel == 1 && it.in == it.out) status = FFT_ERR_UNSUPPORTED;
+    refs.push_back(Ref{p, it.direction == FFT_FORWARD ? 0 : 1, i});
+  }
+  if (status != FFT_OK) {
+    batch_release(b);
+    return status;
+  }
+  // order: persistent-kernel groups (largest N first), then the large groups
+  std::stable_sort(refs.begin(), refs.end(), [](const Ref &a, const Ref &c) {
+    const bool la = a.plan->kernel != 0, lc = c.plan->kernel != 0;
+    if (la != lc) return la < lc;
+    if (a.plan->log2n != c.plan->log2n) return a.plan->log2n > c.plan->log2n;
+    if (a.plan != c.plan) return a.plan < c.plan;
+    return a.dir < c.dir;
+  });
+  std::vector<BatchItem> h_items((size_t)count);
+  std::vector<BatchTile> h_tiles;
+  for (int64_t i = 0; i < count; ++i) h_items[(size_t)i] = BatchItem{items[refs[(size_t)i].index].in, items[refs[(size_t)i].index].out};
+  for (int64_t i = 0; i < count;) {
+    const Ref &r = refs[(size_t)i];
+    int64_t j = i;
+    while (j < count && refs[(size_t)j].plan == r.plan && refs[(size_t)j].dir == r.dir) ++j;
+    if (r.plan->kernel == 0) {
+      const int cap = batch_tile_capacity(r.plan->prec, r.plan->log2n);
+      for (int64_t k = i; k < j; k += cap) {
+        BatchTile t{};
+        t.path = batch_path_code(r.plan->prec, r.plan->log2n, r.plan->scale[r.dir] != 0);
+        t.count = (uint32_t)std::min<int64_t>(cap, j - k);
+        t.first = (uint32_t)k;
+        t.twp = r.plan->twp[r.dir];
+        h_tiles.push_back(t);
+      }
+    } else {
+      b->large.push_back(fft_batch::Large{r.plan, r.dir, i, j - i});
+    }
+    i = j;
+  }
+  b->ntiles = (int)h_tiles.size();
+  do {
+    if (count > 0) {
+      if ((e = cudaMalloc(&b->d_items, sizeof(BatchItem) * (size_t)count)) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc items"); break; }
+      if ((e = cudaMemcpy(b->d_items, h_items.data(), sizeof(BatchItem) * (size_t)count, cudaMemcpyHostToDevice)) != cudaSuccess) { status = cuda_fail(e, "copy items"); break; }
+      b->device_bytes += (int64_t)(sizeof(BatchItem) * (size_t)count);
+    }
+    if (b->ntiles > 0) {
+      if ((e = cudaMalloc(&b->d_tiles, sizeof(BatchTile) * h_tiles.size())) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc tiles"); break; }
+      if ((e = cudaMemcpy(b->d_tiles, h_tiles.data(), sizeof(BatchTile) * h_tiles.size(), cudaMemcpyHostToDevice)) != cudaSuccess) { status = cuda_fail(e, "copy tiles"); break; }
+      if ((e = cudaMalloc(&b->d_counter, sizeof(unsigned))) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc counter"); break; }
+      if ((e = prepare_batch_kernel(&b->grid)) != cudaSuccess) { status = cuda_fail(e, "batch kernel attributes"); break; }
+      b->device_bytes += (int64_t)(sizeof(BatchTile) * h_tiles.size() + sizeof(unsigned));
+    }
+  } while (0);
+  if (status != FFT_OK) {
+    batch_release(b);
+    return status;
+  }
+  for (fft_plan *p : b->plans) b->device_bytes += (int64_t)2 * (p->n / 2 + p->n - 1) * (int64_t)sizeof(uint4);
+  *batch = b;
+  return FFT_OK;
+}
+
+fft_status fft_batch_exec(fft_batch *batch, void *stream) {
+  if (!batch) return FFT_ERR_INVALID_ARG;
+  DeviceGuard guard(batch->device);
+  if (guard.err != cudaSuccess) return cuda_fail(guard.err, "select device");
+  cudaError_t e = batch_enqueue(batch, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "batch launch");
+  return FFT_OK;
+}
+
+fft_status fft_batch_exec_graph(fft_batch *batch, void *stream) {
+  if (!batch) return FFT_ERR_INVALID_ARG;
+  DeviceGuard guard(batch->device);
+  if (guard.err != cudaSuccess) return cuda_fail(guard.err, "select device");
+  cudaError_t e;
+  if (!batch->graph_exec) {
+    if (!batch->capture_stream &&
+        (e = cudaStreamCreateWithFlags(&batch->capture_stream, cudaStreamNonBlocking)) != cudaSuccess)
+      return cuda_fail(e, "capture stream");
+    if ((e = cudaStreamBeginCapture(batch->capture_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+      return cuda_fail(e, "begin capture");
+    cudaError_t le = batch_enqueue(batch, batch->capture_stream);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(batch->capture_stream, &g);
+    if (le != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return cuda_fail(le, "batch launch during capture");
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "end capture");
+    if ((e = cudaGraphInstantiate(&batch->graph_exec, g, 0)) != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return cuda_fail(e, "graph instantiate");
+    }
+    batch->graph = g;
+  }
+  if ((e = cudaGraphLaunch(batch->graph_exec, (cudaStream_t)stream)) != cudaSuccess)
+    return cuda_fail(e, "graph launch");
+  return FFT_OK;
+}
+
+fft_status fft_batch_get_info(const fft_batch *batch, fft_batch_info *info) {
+  if (!batch || !info) return FFT_ERR_INVALID_ARG;
+  memset(info, 0, sizeof *info);
+  info->items = batch->count;
+  info->plans = (int32_t)batch->plans.size();
+  info->tiles = batch->ntiles;
+  info->persistent_blocks = batch->ntiles > 0 ? std::min(batch->grid, batch->ntiles) : 0;
+  info->large_groups = (int32_t)batch->large.size();
+  int launches = batch->ntiles > 0 ? 1 : 0;
+  for (const auto &g : batch->large) launches += g.plan->kernel == 1 ? 2 : 1;
+  info->launches = launches;
+  info->graph_ready = batch->graph_exec != nullptr;
+  info->device_bytes = batch->device_bytes;
+  return FFT_OK;
+}
+
+fft_status fft_batch_destroy(fft_batch *batch) {
+  batch_release(batch);
+  return FFT_OK;
 }
 
 }  // extern "C"

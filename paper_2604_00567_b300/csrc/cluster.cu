@@ -74,10 +74,9 @@ struct Clus {
   static_assert(GC1 % P2::T == 0, "a thread's phase-2 reads never straddle two owners");
 };
 
-template <int PREC, int LOG2N, int LOG2K, bool SCALED>
+template <int PREC, int LOG2N, int LOG2K, bool SCALED, class IO>
 __global__ void __cluster_dims__(1 << LOG2K, 1, 1) __launch_bounds__(Clus<PREC, LOG2N, LOG2K, SCALED>::TPB, 2)
-    cluster_fft_kernel(const typename Elem<PREC>::T *in, typename Elem<PREC>::T *out, int64_t batch,
-                       const uint4 *__restrict__ twp) {
+    cluster_fft_kernel(const IO io, int64_t batch, const uint4 *__restrict__ twp) {
   using K = Clus<PREC, LOG2N, LOG2K, SCALED>;
   using E = typename K::E;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -94,7 +93,7 @@ __global__ void __cluster_dims__(1 << LOG2K, 1, 1) __launch_bounds__(Clus<PREC, 
     const int lg = threadIdx.x % K::GC1;
     const int tid = threadIdx.x / K::GC1;
     const int64_t g = (int64_t)rank * K::GC1 + lg;
-    const E *src = in + tr * K::N + g;
+    const E *src = io.src(tr) + g;
     static_for<0, K::R>([&](auto p_) {
       constexpr int p = decltype(p_)::value;
       v[p] = cl_ldcs(src + (int64_t)(tid + p * K::P1::T) * K::M2);
@@ -130,7 +129,7 @@ __global__ void __cluster_dims__(1 << LOG2K, 1, 1) __launch_bounds__(Clus<PREC, 
     });
     cluster.sync();   // every remote read done before the buffer is reused
     auto at = [&](int o) { return lg * K::M2 + (o ^ (lg & 31)); };
-    E *dst = out + tr * K::N + gp;
+    E *dst = io.dst(tr) + gp;
     K::P2::template run<false>(
         v, tid, gp, K::LS1, twp, [&](int idx, E val) { sm[at(idx)] = val; }, [&](int idx) { return sm[at(idx)]; },
         [] { __syncthreads(); }, [&](int o, E val) { cl_stcs(dst + (int64_t)o * K::M1, val); });
@@ -146,27 +145,38 @@ int cluster_log2k(int prec, int log2n) {
 }
 
 template <int PREC, int LOG2N, int LOG2K, bool SCALED>
-static cudaError_t launch_cluster_one(const void *in, void *out, int64_t batch, const uint4 *twp,
-                                      cudaStream_t stream) {
+static cudaError_t launch_cluster_one(const void *in, void *out, const BatchItem *items, int64_t batch,
+                                      const uint4 *twp, cudaStream_t stream) {
   using K = Clus<PREC, LOG2N, LOG2K, SCALED>;
   using E = typename K::E;
   const int64_t blocks = batch * K::K;
   if (blocks > 0x7FFFFFFF) return cudaErrorInvalidConfiguration;
-  cluster_fft_kernel<PREC, LOG2N, LOG2K, SCALED><<<(unsigned)blocks, K::TPB, K::SMEM, stream>>>(
-      static_cast<const E *>(in), static_cast<E *>(out), batch, twp);
+  if (items) {
+    cluster_fft_kernel<PREC, LOG2N, LOG2K, SCALED, GatherIO<E>><<<(unsigned)blocks, K::TPB, K::SMEM, stream>>>(
+        GatherIO<E>{items}, batch, twp);
+  } else {
+    cluster_fft_kernel<PREC, LOG2N, LOG2K, SCALED, ContigIO<E>><<<(unsigned)blocks, K::TPB, K::SMEM, stream>>>(
+        ContigIO<E>{static_cast<const E *>(in), static_cast<E *>(out), K::N}, batch, twp);
+  }
   return cudaGetLastError();
+}
+
+template <class F>
+static cudaError_t prepare_cluster_kernel(F kern, int smem) {
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
 }
 
 template <int PREC, int LOG2N, int LOG2K>
 static cudaError_t prepare_cluster_one() {
   using K = Clus<PREC, LOG2N, LOG2K, false>;
-  for (auto kern : {cluster_fft_kernel<PREC, LOG2N, LOG2K, false>, cluster_fft_kernel<PREC, LOG2N, LOG2K, true>}) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-    if (e != cudaSuccess) return e;
-  }
-  return cudaSuccess;
+  using E = typename K::E;
+  cudaError_t e;
+  if ((e = prepare_cluster_kernel(cluster_fft_kernel<PREC, LOG2N, LOG2K, false, ContigIO<E>>, K::SMEM)) != cudaSuccess) return e;
+  if ((e = prepare_cluster_kernel(cluster_fft_kernel<PREC, LOG2N, LOG2K, true, ContigIO<E>>, K::SMEM)) != cudaSuccess) return e;
+  if ((e = prepare_cluster_kernel(cluster_fft_kernel<PREC, LOG2N, LOG2K, false, GatherIO<E>>, K::SMEM)) != cudaSuccess) return e;
+  return prepare_cluster_kernel(cluster_fft_kernel<PREC, LOG2N, LOG2K, true, GatherIO<E>>, K::SMEM);
 }
 
 cudaError_t prepare_cluster(int prec, int log2n) {
@@ -183,12 +193,12 @@ cudaError_t prepare_cluster(int prec, int log2n) {
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_cluster(int prec, int log2n, bool scaled, const void *in, void *out, int64_t batch,
-                           const uint4 *twp, cudaStream_t stream) {
-#define DSFFT_CL(P, L, LK)                                                                   \
-  case P * 100 + L:                                                                          \
-    return scaled ? launch_cluster_one<P, L, LK, true>(in, out, batch, twp, stream)          \
-                  : launch_cluster_one<P, L, LK, false>(in, out, batch, twp, stream);
+cudaError_t launch_cluster(int prec, int log2n, bool scaled, const void *in, void *out, const BatchItem *items,
+                           int64_t batch, const uint4 *twp, cudaStream_t stream) {
+#define DSFFT_CL(P, L, LK)                                                                    \
+  case P * 100 + L:                                                                           \
+    return scaled ? launch_cluster_one<P, L, LK, true>(in, out, items, batch, twp, stream)   \
+                  : launch_cluster_one<P, L, LK, false>(in, out, items, batch, twp, stream);
   switch (prec * 100 + log2n) {
     DSFFT_CL(kFP32, 15, 2)
     DSFFT_CL(kFP32, 16, 3)

@@ -52,6 +52,30 @@ __device__ __forceinline__ void static_for(F &&f) {
   }
 }
 
+// Streaming (evict-first) loads and stores of signal data: every element is
+// touched once, so it should not displace the twiddle table in L1/L2.
+__device__ __forceinline__ float2 ldcs(const float2 *p) { return __ldcs(p); }
+__device__ __forceinline__ uint32_t ldcs(const uint32_t *p) { return __ldcs(reinterpret_cast<const unsigned int *>(p)); }
+__device__ __forceinline__ void stcs(float2 *p, float2 v) { __stcs(p, v); }
+__device__ __forceinline__ void stcs(uint32_t *p, uint32_t v) { __stcs(reinterpret_cast<unsigned int *>(p), v); }
+
+// Where the signals of transform k live: contiguous batches (transform k at
+// k N) or a gathered list of per-transform pointers (mixed batches).
+template <class E>
+struct ContigIO {
+  const E *in;
+  E *out;
+  int64_t n;
+  __device__ __forceinline__ const E *src(int64_t k) const { return in + k * n; }
+  __device__ __forceinline__ E *dst(int64_t k) const { return out + k * n; }
+};
+template <class E>
+struct GatherIO {
+  const BatchItem *items;
+  __device__ __forceinline__ const E *src(int64_t k) const { return static_cast<const E *>(items[k].in); }
+  __device__ __forceinline__ E *dst(int64_t k) const { return static_cast<E *>(items[k].out); }
+};
+
 // Storage type of one complex element.
 template <int PREC> struct Elem;
 template <> struct Elem<kFP32> { using T = float2; };

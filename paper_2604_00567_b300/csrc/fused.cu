@@ -1,149 +1,9 @@
-// fused.cu — one-launch FFT for N <= 2^14: every pass of a transform runs on
-// chip, so each signal is read from HBM once and written once.
-//
-// The m = log2 N radix-2 Stockham passes (Section IV) are grouped into
-// stages of up to r = log2 R passes.  Before pass P the Stockham array is
-// Z_P[s 2^P + j] (s in [0, N/2^P), j in [0, 2^P)); pass P combines
-// a = Z_P[s 2^P + j], b = Z_P[N/2 + s 2^P + j] with W = table[j N/2^(P+1)]
-// into Z_{P+1}[s 2^(P+1) + j] = a + W b, Z_{P+1}[s 2^(P+1) + 2^P + j] = a - W b.
-// A stage of rho passes starting at P only mixes, for each (s_lo, j), the
-// 2^rho values Z_P[(s_lo + q N/2^(P+rho)) 2^P + j], q in [0, 2^rho), so one
-// thread keeps them in registers and runs the rho passes with the exact
-// butterflies of the radix-2 algorithm (same operands, same twiddles, same
-// rounding): the result is bit-identical to pass-by-pass execution.  Stages
-// exchange data through shared memory.  Thread `tid` of a transform reads
-// Z_P[tid + p T] (p in [0, R), T = N/R threads), which is coalesced for the
-// first stage (from HBM) and bank-conflict-free for the others; the last
-// stage writes X[tid + p T] (coalesced).
-//
-// Twiddles come from the plan's per-pass table: pass p uses entries
-// twp[2^p - 1 + j] = table[j N/2^(p+1)], j in [0, 2^p) (exact copies of the
-// rounded entries), so the lanes of a warp, which hold consecutive j, read
-// consecutive 16-byte entries.
-#include "common.cuh"
-#include "internal.h"
+// fused.cu — one-launch FFT of a batch of equal-size signals, N <= 2^14:
+// every pass of a transform runs on chip, so each signal is read from HBM
+// once and written once (stage structure in fused.cuh).
+#include "fused.cuh"
 
 namespace dsfft {
-
-// Streaming (evict-first) loads and stores of signal data: every element is
-// touched once, so it should not displace the twiddle table in L1/L2.
-__device__ __forceinline__ float2 ldcs(const float2 *p) { return __ldcs(p); }
-__device__ __forceinline__ uint32_t ldcs(const uint32_t *p) { return __ldcs(reinterpret_cast<const unsigned int *>(p)); }
-__device__ __forceinline__ void stcs(float2 *p, float2 v) { __stcs(p, v); }
-__device__ __forceinline__ void stcs(uint32_t *p, uint32_t v) { __stcs(reinterpret_cast<unsigned int *>(p), v); }
-
-template <int PREC, int LOG2N, int LOG2R, bool SCALED>
-struct Fused {
-  using E = typename Elem<PREC>::T;
-  static constexpr int N = 1 << LOG2N;
-  static constexpr int R = 1 << LOG2R;
-  static constexpr int T = N / R;                        // threads per transform
-  static constexpr int TPC = T >= 256 ? 1 : 256 / T;     // transforms per block
-  static constexpr int TPB = T * TPC;
-  static constexpr int NSTAGES = (LOG2N + LOG2R - 1) / LOG2R;
-  static constexpr int PADN = N + (N >> 5);              // one pad element per 32 (conflict-free
-                                                         // exchanges for R = 32 (4-byte) / R = 16 (8-byte))
-  static constexpr int SMEM = NSTAGES > 1 ? TPC * PADN * (int)sizeof(E) : 0;
-  // Blocks per SM the register allocation must allow: 1024 threads' worth
-  // (at most 64 registers per thread), so at least half the SM's warps can
-  // be resident.
-  static constexpr int MINB = TPB >= 1024 ? 1 : 1024 / TPB;
-
-  static __device__ __forceinline__ int pad(int idx) { return idx + (idx >> 5); }
-
-  // Exchange barrier of one transform's T threads: a warp barrier when they
-  // share a warp, a named barrier per transform when a block holds several
-  // multi-warp transforms (so transforms do not wait for each other), else
-  // the block barrier.
-  static __device__ __forceinline__ void sync(int lt) {
-    if constexpr (T <= 32) {
-      __syncwarp();
-    } else if constexpr (TPC > 1) {
-      asm volatile("bar.sync %0, %1;" ::"r"(1 + lt), "r"(T) : "memory");
-    } else {
-      __syncthreads();
-    }
-  }
-  static_assert(TPC <= 15 || T <= 32, "named barriers 1..15");
-
-  // rho radix-2 passes starting at pass P on the registers of one thread.
-  template <int P, int RHO>
-  static __device__ __forceinline__ void compute(E (&v)[R], int tid, const uint4 *__restrict__ tw,
-                                                 const Stage0Twiddles &tw0) {
-    constexpr int C = R >> RHO;   // independent groups per thread
-    static_for<0, C>([&](auto c_) {
-      constexpr int c = decltype(c_)::value;
-      const int g = tid + c * T;
-      const int j = g & ((1 << P) - 1);
-      static_for<0, RHO>([&](auto i_) {
-        constexpr int i = decltype(i_)::value;
-        constexpr int half = 1 << (RHO - 1 - i);
-        static_for<0, (1 << i)>([&](auto ql_) {
-          constexpr int ql = decltype(ql_)::value;
-          // pass P+i, j_full = j + ql 2^P; the first stage (j = 0) reads the
-          // constant bank
-          uint4 e;
-          if constexpr (P == 0) e = tw0.e[((1 << i) - 1) + ql];
-          else e = __ldg(tw + ((1 << (P + i)) - 1) + j + (ql << P));
-          constexpr int qtop = bitrev(ql, i) << (RHO - i);
-          static_for<0, half>([&](auto qh_) {
-            constexpr int q = qtop | decltype(qh_)::value;
-            Bfly<PREC, SCALED>::run(v[c + q * C], v[c + (q + half) * C], e);
-          });
-        });
-      });
-    });
-  }
-
-  template <int S>
-  static __device__ __forceinline__ void stages(E (&v)[R], E *sm, int tid, int lt, const uint4 *__restrict__ tw,
-                                                const Stage0Twiddles &tw0, E *dst, bool active) {
-    constexpr int P = S * LOG2R;
-    constexpr int RHO = (LOG2N - P) < LOG2R ? (LOG2N - P) : LOG2R;
-    constexpr int C = R >> RHO;
-    if constexpr (S > 0) {
-      // pad(tid + p T) = pad(tid) + p T + p T / 32 when 32 | T: one base
-      // address plus compile-time offsets
-      const int pt = pad(tid);
-      static_for<0, R>([&](auto p_) {
-        constexpr int p = decltype(p_)::value;
-        if constexpr (T % 32 == 0) v[p] = sm[pt + p * T + ((p * T) >> 5)];
-        else v[p] = sm[pad(tid + p * T)];
-      });
-    }
-    compute<P, RHO>(v, tid, tw, tw0);
-    if constexpr (P + RHO == LOG2N) {
-      if (active) {
-        static_for<0, C>([&](auto c_) {
-          constexpr int c = decltype(c_)::value;
-          static_for<0, (1 << RHO)>([&](auto q_) {
-            constexpr int q = decltype(q_)::value;
-            stcs(dst + tid + c * T + (bitrev(q, RHO) << P), v[c + q * C]);
-          });
-        });
-      }
-    } else {
-      if constexpr (S > 0) sync(lt);   // previous exchange fully read
-      // pad(base + off) = pad(base) + off + off / 32 when off is a multiple
-      // of 32 (P >= 5) or base is and off < 32 (P = 0, RHO = 5)
-      constexpr bool FOLD = P >= 5 || (P == 0 && RHO == 5);
-      static_for<0, C>([&](auto c_) {
-        constexpr int c = decltype(c_)::value;
-        const int g = tid + c * T;
-        const int base = ((g >> P) << (P + RHO)) + (g & ((1 << P) - 1));
-        const int pb = pad(base);
-        static_for<0, (1 << RHO)>([&](auto q_) {
-          constexpr int q = decltype(q_)::value;
-          constexpr int off = bitrev(q, RHO) << P;
-          if constexpr (FOLD) sm[pb + off + (off >> 5)] = v[c + q * C];
-          else sm[pad(base + off)] = v[c + q * C];
-        });
-      });
-      sync(lt);
-      stages<S + 1>(v, sm, tid, lt, tw, tw0, dst, active);
-    }
-  }
-};
 
 template <int PREC, int LOG2N, int LOG2R, bool SCALED>
 __global__ void __launch_bounds__(Fused<PREC, LOG2N, LOG2R, SCALED>::TPB, Fused<PREC, LOG2N, LOG2R, SCALED>::MINB)
@@ -152,34 +12,15 @@ __global__ void __launch_bounds__(Fused<PREC, LOG2N, LOG2R, SCALED>::TPB, Fused<
   using K = Fused<PREC, LOG2N, LOG2R, SCALED>;
   using E = typename K::E;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int lt = threadIdx.x / K::T;
-  const int tid = threadIdx.x % K::T;
-  const int64_t tr = (int64_t)blockIdx.x * K::TPC + lt;
-  const bool active = tr < batch;
-  E *sm = reinterpret_cast<E *>(smem_raw) + lt * K::PADN;
-  E v[K::R];
-  const E *src = in + tr * K::N;
-  if (active) {
-    static_for<0, K::R>([&](auto p_) {
-      constexpr int p = decltype(p_)::value;
-      v[p] = ldcs(src + tid + p * K::T);
-    });
-  } else {
-    static_for<0, K::R>([&](auto p_) { v[decltype(p_)::value] = E{}; });
-  }
-  K::template stages<0>(v, sm, tid, lt, tw, tw0, out + tr * K::N, active);
+  const int64_t first = (int64_t)blockIdx.x * K::TPC;
+  const int64_t left = batch - first;
+  const int count = left < K::TPC ? (int)left : K::TPC;
+  const ContigIO<E> io{in + first * K::N, out + first * K::N, K::N};
+  K::run_tile(io, count, tw, [&](int i) { return tw0.e[i]; }, reinterpret_cast<E *>(smem_raw));
 }
 
 // ---------------------------------------------------------------------------
 // dispatch
-
-// Points per thread: 32 four-byte (FP16/BF16) or 16 eight-byte (FP32)
-// elements, so a thread's register block is 32 registers and every exchange
-// is bank-conflict-free with the one-in-32 padding.
-constexpr int fused_log2r(int prec, int log2n) {
-  const int r = prec == kFP32 ? 4 : 5;
-  return log2n < r ? log2n : r;
-}
 
 template <int PREC, int LOG2N, bool SCALED>
 static cudaError_t launch_one(const void *in, void *out, int64_t batch, const uint4 *tw, const Stage0Twiddles &tw0,

@@ -9,6 +9,27 @@ namespace dsfft {
 
 enum Prec : int { kFP32 = 0, kFP16 = 1, kBF16 = 2 };
 
+// One transform of a mixed batch: device pointers to its input and output.
+struct BatchItem {
+  const void *in;
+  void *out;
+};
+
+// One unit of work of the persistent batch kernel: `count` transforms of
+// one size/precision/direction, items [first, first + count).
+struct BatchTile {
+  uint32_t path;      // batch_path_code(prec, log2n, scaled)
+  uint32_t count;
+  uint32_t first;
+  uint32_t reserved;
+  const uint4 *twp;   // per-pass twiddle table of the direction
+  uint64_t reserved2;
+};
+
+__host__ __device__ constexpr uint32_t batch_path_code(int prec, int log2n, bool scaled) {
+  return (uint32_t)((((prec * 32) + log2n) << 1) | (scaled ? 1 : 0));
+}
+
 constexpr int kMaxLog2N = 24;
 constexpr int kFusedMaxLog2N = 14;   // whole transform staged on chip
 
@@ -46,15 +67,22 @@ cudaError_t launch_fused(int prec, int log2n, bool scaled, const void *in, void 
 // `in` and `out` must differ; sweep 2 runs in place on `out`.
 void sweep_split(int log2n, int *ls1, int *ls2);
 cudaError_t prepare_sweeps(int prec, int log2n);
-cudaError_t launch_sweeps(int prec, int log2n, bool scaled, const void *in, void *out, int64_t batch,
-                          const uint4 *twp, cudaStream_t stream);
+// `items` (device array, one per transform) replaces in/out when non-null.
+cudaError_t launch_sweeps(int prec, int log2n, bool scaled, const void *in, void *out, const BatchItem *items,
+                          int64_t batch, const uint4 *twp, cudaStream_t stream);
 
 // 2^15 <= N <= 2^17 (FP16/BF16) or <= 2^16 (FP32): one launch on a cluster
 // of 2^cluster_log2k CTAs whose distributed shared memory holds the
 // transform between the two halves of the passes.  -1 = not handled.
 int cluster_log2k(int prec, int log2n);
 cudaError_t prepare_cluster(int prec, int log2n);
-cudaError_t launch_cluster(int prec, int log2n, bool scaled, const void *in, void *out, int64_t batch,
-                           const uint4 *twp, cudaStream_t stream);
+cudaError_t launch_cluster(int prec, int log2n, bool scaled, const void *in, void *out, const BatchItem *items,
+                           int64_t batch, const uint4 *twp, cudaStream_t stream);
+
+// Persistent mixed-size batch kernel (N <= 2^14, any precision).
+int batch_tile_capacity(int prec, int log2n);
+cudaError_t prepare_batch_kernel(int *grid);
+cudaError_t launch_batch_kernel(const BatchTile *tiles, int ntiles, const BatchItem *items, unsigned *counter,
+                                int grid, cudaStream_t stream);
 
 }  // namespace dsfft

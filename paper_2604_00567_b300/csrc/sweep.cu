@@ -142,10 +142,11 @@ struct Sweep {
   }
 };
 
-template <int PREC, int LS, bool SCALED, bool LAST>
+// Sweep 1 reads io.src and writes io.dst; sweep 2 (LAST) reads and writes
+// io.dst in place.
+template <int PREC, int LS, bool SCALED, bool LAST, class IO>
 __global__ void __launch_bounds__(Sweep<PREC, LS, SCALED, LAST>::TPB)
-    sweep_fft_kernel(const typename Elem<PREC>::T *in, typename Elem<PREC>::T *out, int64_t batch, int log2n,
-                     int P0, const uint4 *__restrict__ twp) {
+    sweep_fft_kernel(const IO io, int64_t batch, int log2n, int P0, const uint4 *__restrict__ twp) {
   using K = Sweep<PREC, LS, SCALED, LAST>;
   using E = typename K::E;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -163,8 +164,8 @@ __global__ void __launch_bounds__(Sweep<PREC, LS, SCALED, LAST>::TPB)
   x.jg = x.g & ((1LL << P0) - 1);
   const bool active = tr < batch;
   E v[K::R];
-  const E *src = in + tr * n + x.g;
   if (active) {
+    const E *src = (LAST ? io.dst(tr) : io.src(tr)) + x.g;
     static_for<0, K::R>([&](auto p_) {
       constexpr int p = decltype(p_)::value;
       v[p] = sw_ldcs(src + (int64_t)(x.tid + p * K::T) * S);
@@ -174,7 +175,7 @@ __global__ void __launch_bounds__(Sweep<PREC, LS, SCALED, LAST>::TPB)
   }
   // sweep 2 (LAST) writes group g's outputs at g + o S; sweep 1 writes the
   // block's contiguous range starting at g0 2^LS
-  E *dst = LAST ? out + tr * n : out + tr * n + (g0 << LS);
+  E *dst = !active ? nullptr : LAST ? io.dst(tr) : io.dst(tr) + (g0 << LS);
   K::template stages<0>(v, sm, x, twp, dst, S, active);
 }
 
@@ -182,29 +183,42 @@ __global__ void __launch_bounds__(Sweep<PREC, LS, SCALED, LAST>::TPB)
 // dispatch: LS in [7, 12] (N = 2^15 .. 2^24 split as ceil(m/2) + floor(m/2))
 
 template <int PREC, int LS, bool SCALED, bool LAST>
-static cudaError_t launch_sweep_one(const void *in, void *out, int64_t batch, int log2n, int P0, const uint4 *twp,
-                                    cudaStream_t stream) {
+static cudaError_t launch_sweep_one(const void *in, void *out, const BatchItem *items, int64_t batch, int log2n,
+                                    int P0, const uint4 *twp, cudaStream_t stream) {
   using K = Sweep<PREC, LS, SCALED, LAST>;
   using E = typename K::E;
   const int64_t S = 1LL << (log2n - LS);
   if (S < K::G) return cudaErrorInvalidValue;
   const int64_t blocks = batch * (S >> K::LOG2G);
   if (blocks > 0x7FFFFFFF) return cudaErrorInvalidConfiguration;
-  sweep_fft_kernel<PREC, LS, SCALED, LAST><<<(unsigned)blocks, K::TPB, K::SMEM, stream>>>(
-      static_cast<const E *>(in), static_cast<E *>(out), batch, log2n, P0, twp);
+  if (items) {
+    sweep_fft_kernel<PREC, LS, SCALED, LAST, GatherIO<E>><<<(unsigned)blocks, K::TPB, K::SMEM, stream>>>(
+        GatherIO<E>{items}, batch, log2n, P0, twp);
+  } else {
+    sweep_fft_kernel<PREC, LS, SCALED, LAST, ContigIO<E>><<<(unsigned)blocks, K::TPB, K::SMEM, stream>>>(
+        ContigIO<E>{static_cast<const E *>(in), static_cast<E *>(out), 1LL << log2n}, batch, log2n, P0, twp);
+  }
   return cudaGetLastError();
+}
+
+template <class F>
+static cudaError_t prepare_sweep_kernel(F kern, int smem) {
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
 }
 
 template <int PREC, int LS, bool SCALED, bool LAST>
 static cudaError_t prepare_sweep_one() {
   using K = Sweep<PREC, LS, SCALED, LAST>;
-  auto kern = sweep_fft_kernel<PREC, LS, SCALED, LAST>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM);
+  using E = typename K::E;
+  cudaError_t e = prepare_sweep_kernel(sweep_fft_kernel<PREC, LS, SCALED, LAST, ContigIO<E>>, K::SMEM);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  return prepare_sweep_kernel(sweep_fft_kernel<PREC, LS, SCALED, LAST, GatherIO<E>>, K::SMEM);
 }
 
-using SweepFn = cudaError_t (*)(const void *, void *, int64_t, int, int, const uint4 *, cudaStream_t);
+using SweepFn = cudaError_t (*)(const void *, void *, const BatchItem *, int64_t, int, int, const uint4 *,
+                                cudaStream_t);
 using SweepPrepFn = cudaError_t (*)();
 
 template <int PREC, bool SCALED, bool LAST, int... LSs>
@@ -251,8 +265,8 @@ cudaError_t prepare_sweeps(int prec, int log2n) {
   return cudaSuccess;
 }
 
-cudaError_t launch_sweeps(int prec, int log2n, bool scaled, const void *in, void *out, int64_t batch,
-                          const uint4 *twp, cudaStream_t stream) {
+cudaError_t launch_sweeps(int prec, int log2n, bool scaled, const void *in, void *out, const BatchItem *items,
+                          int64_t batch, const uint4 *twp, cudaStream_t stream) {
   int ls1, ls2;
   sweep_split(log2n, &ls1, &ls2);
   if (ls1 < 7 || ls1 > 12 || ls2 < 7 || ls2 > 12) return cudaErrorInvalidValue;
@@ -260,9 +274,9 @@ cudaError_t launch_sweeps(int prec, int log2n, bool scaled, const void *in, void
     return prec == kFP32 ? SweepSet<kFP32>::get(scaled, last, ls)
            : prec == kFP16 ? SweepSet<kFP16>::get(scaled, last, ls) : SweepSet<kBF16>::get(scaled, last, ls);
   };
-  cudaError_t e = get(false, ls1)(in, out, batch, log2n, 0, twp, stream);
+  cudaError_t e = get(false, ls1)(in, out, items, batch, log2n, 0, twp, stream);
   if (e != cudaSuccess) return e;
-  return get(true, ls2)(out, out, batch, log2n, ls1, twp, stream);
+  return get(true, ls2)(out, out, items, batch, log2n, ls1, twp, stream);
 }
 
 }  // namespace dsfft

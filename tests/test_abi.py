@@ -92,3 +92,28 @@ def test_status_codes_match_binding():
     hdr = open(os.path.join(ROOT, "include", "dsfft.h")).read()
     for code, name in dsfft.STATUS.items():
         assert re.search(rf"\b{name}\s*=\s*{code}\b", hdr), name
+
+
+def test_batch_validation_without_gpu(lib):
+    """fft_batch_create rejects bad items before any CUDA call."""
+    import paper_2604_00567_b300 as dsfft
+    h = ctypes.c_void_p()
+    arr = (dsfft.BatchItemC * 2)()
+    for a in arr:
+        a.n, a.precision, a.factorization, a.direction = 1024, 0, 2, -1
+        a.in_, a.out = 0x1000, 0x2000
+    arr[1].n = 1000
+    assert lib.fft_batch_create(ctypes.byref(h), arr, 2, None) == 2
+    arr[1].n = 1024
+    arr[1].direction = 0
+    assert lib.fft_batch_create(ctypes.byref(h), arr, 2, None) == 1
+    arr[1].direction = 1
+    arr[1].in_ = None
+    assert lib.fft_batch_create(ctypes.byref(h), arr, 2, None) == 1
+    arr[1].in_ = 0x1004    # not 8-byte aligned for complex64
+    assert lib.fft_batch_create(ctypes.byref(h), arr, 2, None) == 1
+    assert lib.fft_batch_create(None, arr, 2, None) == 1
+    assert lib.fft_batch_create(ctypes.byref(h), None, 2, None) == 1
+    assert lib.fft_batch_create(ctypes.byref(h), arr, -1, None) == 1
+    assert lib.fft_batch_exec(None, None) == 1
+    assert lib.fft_batch_destroy(None) == 0
