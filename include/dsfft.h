@@ -225,6 +225,40 @@ DSFFT_API fft_status fft_batch_get_info(const fft_batch *batch, fft_batch_info *
  * using it must have completed. */
 DSFFT_API fft_status fft_batch_destroy(fft_batch *batch);
 
+/* ------------------------------------------------------------------------ */
+/* A mixed batch that allocates no device memory.  This entry point has no
+ * counterpart in the paper; it exists for callers that cannot call cudaMalloc
+ * where they transform — a host program that owns all device memory through
+ * its own fixed pool, or a latency-bound loop where cudaMalloc/cudaFree would
+ * stall on their implicit synchronisation.  It runs the same kernels as
+ * fft_batch_exec, with the work descriptors and work counter in one fixed
+ * device array of the library (about 192 KB, present in every GPU that loads
+ * the library until exit) instead of memory the batch allocates.
+ *   - `items`: `count` <= FFT_NOALLOC_MAX_ITEMS transforms, each with a plan
+ *     created beforehand (fft_plan_create allocates; do that first), a
+ *     direction and device input/output pointers (element-aligned; in == out
+ *     is refused for plans on the HBM-sweep path).  More items:
+ *     FFT_ERR_INVALID_SIZE.  All plans must be on one device.
+ *   - Asynchronous on `stream`; the descriptors are copied from host memory
+ *     before the call returns.
+ *   - The first call on a device also looks up the device address of the
+ *     array and sets the kernel's attributes; make that first call before
+ *     any stream capture.
+ *   - Every call reuses the same array (the work counter is cleared at the
+ *     start of each call); calls whose work overlaps on the GPU, e.g. on two
+ *     streams, race on it — order them on one stream. */
+#define FFT_NOALLOC_MAX_ITEMS 4096
+
+typedef struct fft_noalloc_item {
+    const fft_plan *plan;
+    int32_t direction;        /* fft_direction */
+    int32_t reserved;         /* must be zero */
+    const void *in;
+    void *out;
+} fft_noalloc_item;
+
+DSFFT_API fft_status fft_exec_batch_noalloc(const fft_noalloc_item *items, int64_t count, void *stream);
+
 /* Static description of a status code. */
 DSFFT_API const char *fft_status_string(fft_status status);
 

@@ -63,6 +63,14 @@ class BatchItemC(ctypes.Structure):
                 ("in_", ctypes.c_void_p), ("out", ctypes.c_void_p)]
 
 
+class NoAllocItemC(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("direction", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("in_", ctypes.c_void_p), ("out", ctypes.c_void_p)]
+
+
+NOALLOC_MAX_ITEMS = 4096
+
+
 class BatchInfo(ctypes.Structure):
     _fields_ = [("items", ctypes.c_int64), ("plans", ctypes.c_int32), ("tiles", ctypes.c_int32),
                 ("persistent_blocks", ctypes.c_int32), ("large_groups", ctypes.c_int32),
@@ -101,9 +109,11 @@ def lib():
             L.fft_batch_exec_graph.argtypes = [P, P]
             L.fft_batch_get_info.argtypes = [P, ctypes.POINTER(BatchInfo)]
             L.fft_batch_destroy.argtypes = [P]
+            L.fft_exec_batch_noalloc.argtypes = [ctypes.POINTER(NoAllocItemC), i64, P]
             for name in ("fft_plan_opts_init", "fft_plan_create", "fft_plan_destroy", "fft_exec",
                          "fft_plan_get_table", "fft_plan_get_info", "fft_twiddle_fp64", "fft_batch_create",
-                         "fft_batch_exec", "fft_batch_exec_graph", "fft_batch_get_info", "fft_batch_destroy"):
+                         "fft_batch_exec", "fft_batch_exec_graph", "fft_batch_get_info", "fft_batch_destroy",
+                         "fft_exec_batch_noalloc"):
                 getattr(L, name).restype = i32
             _lib = L
     return _lib
@@ -299,6 +309,26 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def exec_batch_noalloc(items, stream=None):
+    """Mixed batch through ``fft_exec_batch_noalloc``, the entry point that
+    allocates no device memory (for callers that cannot call cudaMalloc
+    where they transform: programs that own all device memory through
+    their own pool, or latency-bound loops that must not stall on the
+    allocator).  ``items``: ``(plan, direction, x, out)`` with plans created
+    beforehand and at most ``NOALLOC_MAX_ITEMS`` entries.  The library's
+    fixed descriptor array is shared by all calls: keep calls that could
+    overlap on the GPU on one stream."""
+    items = list(items)
+    arr = (NoAllocItemC * max(1, len(items)))()
+    for i, (plan, direction, x, out) in enumerate(items):
+        arr[i].plan = plan.handle.value
+        arr[i].direction = int(direction)
+        arr[i].reserved = 0
+        arr[i].in_ = x.data_ptr()
+        arr[i].out = out.data_ptr()
+    _check(lib().fft_exec_batch_noalloc(arr, len(items), _stream_handle(stream)), "fft_exec_batch_noalloc")
 
 
 def twiddle_fp64(n: int, factorization: str = "dual_select", lf_eps: float = 1e-7):

@@ -71,6 +71,21 @@ size_t elem_bytes(int prec) { return prec == kFP32 ? 8 : 4; }
 
 }  // namespace
 
+bool dsfft::plan_view(const fft_plan *p, PlanView *v) {
+  if (!p || !v) return false;
+  v->device = p->device;
+  v->kernel = p->kernel;
+  v->prec = p->prec;
+  v->log2n = p->log2n;
+  v->scale[0] = p->scale[0];
+  v->scale[1] = p->scale[1];
+  v->twp[0] = p->twp[0];
+  v->twp[1] = p->twp[1];
+  return true;
+}
+
+void dsfft::set_last_error(const char *msg) { snprintf(g_last_error, sizeof g_last_error, "%s", msg); }
+
 extern "C" {
 
 struct fft_batch {
@@ -131,6 +146,7 @@ void batch_release(fft_batch *b) {
 }
 
 }  // namespace
+
 
 const char *fft_status_string(fft_status s) {
   switch (s) {

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+struct fft_plan;   // the C ABI's opaque plan (defined in api.cu)
+
 namespace dsfft {
 
 enum Prec : int { kFP32 = 0, kFP16 = 1, kBF16 = 2 };
@@ -78,6 +80,17 @@ int cluster_log2k(int prec, int log2n);
 cudaError_t prepare_cluster(int prec, int log2n);
 cudaError_t launch_cluster(int prec, int log2n, bool scaled, const void *in, void *out, const BatchItem *items,
                            int64_t batch, const uint4 *twp, cudaStream_t stream);
+
+// Read-only view of a plan's launch parameters (for entry points outside
+// api.cu); false for a null plan.
+struct PlanView {
+  int device, kernel, prec, log2n;
+  int scale[2];
+  const uint4 *twp[2];
+};
+
+bool plan_view(const ::fft_plan *p, PlanView *v);
+void set_last_error(const char *msg);
 
 // Persistent mixed-size batch kernel (N <= 2^14, any precision).
 int batch_tile_capacity(int prec, int log2n);
