@@ -128,13 +128,22 @@ def barrier(world):
 
 
 def allreduce_max(x: float, world: int) -> float:
+    """Max of x over the ranks (NCCL tensors on the GPU, gloo on the CPU)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_throughput(local_ms: float, units_per_rank: int, world: int):
+    """Replicas only: every rank transforms its own batch.  The job's time is
+    the slowest rank's; the throughput counts every rank's units."""
+    ms = allreduce_max(local_ms, world)
+    return ms, world * units_per_rank / (ms / 1e3)
 
 
 def kernel_source_hash() -> str:
@@ -226,9 +235,9 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier(world)
     clocks = sampler.stop()
-    ms_total = allreduce_max(t_start.elapsed_time(t_end), world)
-    ms_per_step = ms_total / K
     transforms_per_step = sum(batch_for(l) for l in log2ns)
+    ms_total, _ = replica_throughput(t_start.elapsed_time(t_end), transforms_per_step * K, world)
+    ms_per_step = ms_total / K
     value = world * transforms_per_step / (ms_per_step / 1e3)
 
     per_n = {}
