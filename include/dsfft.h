@@ -85,12 +85,32 @@ typedef enum fft_scaling {
     FFT_SCALE_HALF_PER_PASS = 1
 } fft_scaling;
 
+/* Kernel variants a plan can run (all bit-identical; they differ in speed). */
+typedef enum fft_variant {
+    FFT_VARIANT_AUTO = 0,          /* built-in choice, or the autotuner's */
+    FFT_VARIANT_FUSED_WIDE = 1,    /* N <= 2^14: 32 (FP16/BF16) / 16 (FP32) points per thread */
+    FFT_VARIANT_FUSED_NARROW = 2,  /* N <= 2^14: half the points per thread (where
+                                      that keeps a transform within 1024 threads) */
+    FFT_VARIANT_CLUSTER = 3,       /* 2^15 <= N <= 2^17 (FP16/BF16), <= 2^16 (FP32):
+                                      one launch on a thread-block cluster */
+    FFT_VARIANT_SWEEPS = 4         /* N >= 2^15: two HBM sweeps */
+} fft_variant;
+
 typedef struct fft_plan_opts {
     double lf_eps;          /* clamp for FFT_FAC_LINZER_FEIG_CLAMPED (default 1e-7) */
     int32_t scale_forward;  /* fft_scaling of forward transforms */
     int32_t scale_inverse;  /* fft_scaling of inverse transforms */
     int32_t device;         /* CUDA device ordinal; -1 = current device */
-    int32_t reserved[5];    /* must be zero */
+    /* 1: when `variant` is AUTO, time every candidate variant for this
+     * (precision, N) on the plan's GPU at creation (about 128 MiB of scratch
+     * buffers, freed before returning) and keep the fastest; the choice is
+     * cached per GPU model in the JSON file named by the environment variable
+     * DSFFT_AUTOTUNE_CACHE, if set, and reused by later plans. 0: built-in
+     * choice. */
+    int32_t autotune;
+    int32_t variant;        /* fft_variant; a variant the size does not have
+                               gives FFT_ERR_UNSUPPORTED */
+    int32_t reserved[3];    /* must be zero */
 } fft_plan_opts;
 
 typedef struct fft_plan_info {
@@ -111,6 +131,8 @@ typedef struct fft_plan_info {
     int32_t scale_inverse;
     int32_t cos_count;          /* table entries on the cosine path */
     int32_t sin_count;          /* table entries on the sine path */
+    int32_t variant;            /* fft_variant the plan runs */
+    int32_t autotuned;          /* 1 = chosen by timing, 2 = from the cache */
 } fft_plan_info;
 
 typedef struct fft_plan fft_plan;

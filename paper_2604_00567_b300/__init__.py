@@ -41,10 +41,15 @@ class DsfftError(RuntimeError):
         super().__init__(f"{where}: {STATUS.get(status, status)}" + (f" ({detail})" if detail else ""))
 
 
+VARIANTS = {"auto": 0, "fused_wide": 1, "fused_narrow": 2, "cluster": 3, "sweeps": 4}
+VARIANT_NAMES = {v: k for k, v in VARIANTS.items()}
+
+
 class PlanOpts(ctypes.Structure):
     _fields_ = [("lf_eps", ctypes.c_double), ("scale_forward", ctypes.c_int32),
                 ("scale_inverse", ctypes.c_int32), ("device", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("autotune", ctypes.c_int32), ("variant", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -54,7 +59,8 @@ class PlanInfo(ctypes.Structure):
                 ("threads_per_transform", ctypes.c_int32), ("transforms_per_block", ctypes.c_int32),
                 ("table_bytes", ctypes.c_int64), ("element_bytes", ctypes.c_int64),
                 ("scale_forward", ctypes.c_int32), ("scale_inverse", ctypes.c_int32),
-                ("cos_count", ctypes.c_int32), ("sin_count", ctypes.c_int32)]
+                ("cos_count", ctypes.c_int32), ("sin_count", ctypes.c_int32),
+                ("variant", ctypes.c_int32), ("autotuned", ctypes.c_int32)]
 
 
 class BatchItemC(ctypes.Structure):
@@ -136,7 +142,8 @@ class Plan:
 
     def __init__(self, n: int, precision: str = "fp32", factorization: str = "dual_select",
                  lf_eps: float = 1e-7, scale_forward: bool | None = None,
-                 scale_inverse: bool | None = None, device: int | None = None):
+                 scale_inverse: bool | None = None, device: int | None = None,
+                 variant: str = "auto", autotune: bool = False):
         L = lib()
         self.n = int(n)
         self.precision = precision
@@ -150,6 +157,8 @@ class Plan:
             opts.scale_inverse = 1 if scale_inverse else 0
         if device is not None:
             opts.device = int(device)
+        opts.variant = VARIANTS[variant]
+        opts.autotune = 1 if autotune else 0
         self.scale_forward = bool(opts.scale_forward)
         self.scale_inverse = bool(opts.scale_inverse)
         h = ctypes.c_void_p()
@@ -183,7 +192,9 @@ class Plan:
     def info(self) -> dict:
         inf = PlanInfo()
         _check(lib().fft_plan_get_info(self._h, ctypes.byref(inf)), "fft_plan_get_info")
-        return {k: getattr(inf, k) for k, _ in PlanInfo._fields_}
+        d = {k: getattr(inf, k) for k, _ in PlanInfo._fields_}
+        d["variant_name"] = VARIANT_NAMES.get(d["variant"], "?")
+        return d
 
     def element_bytes(self) -> int:
         return 8 if self.precision == "fp32" else 4

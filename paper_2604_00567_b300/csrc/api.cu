@@ -2,10 +2,14 @@
 // creation (FP64 table build on the GPU, rounding once, resident packed
 // tables for both directions), execution dispatch and error reporting.
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
+#include <unistd.h>
 
 #include <algorithm>
 #include <map>
+#include <mutex>
+#include <string>
 #include <tuple>
 #include <vector>
 
@@ -25,7 +29,10 @@ struct fft_plan {
   uint4 *table[2];      // packed tables (N/2 entries), [0] forward, [1] inverse
   uint4 *twp[2];        // per-pass copies (N - 1 entries) read by the kernels
   Stage0Twiddles tw0[2];  // host copy of the first min(N, 32) - 1 per-pass entries
-  int kernel;           // 0 fused
+  int kernel;           // 0 fused, 1 sweeps, 2 cluster
+  bool narrow;          // fused: half-width register block
+  int variant;          // fft_variant
+  int autotuned;        // 0 built-in, 1 timed, 2 cache
   FusedShape shape;
   int cos_count, sin_count;
 };
@@ -59,6 +66,151 @@ struct DeviceGuard {
     if (switched) cudaSetDevice(prev);
   }
 };
+
+bool variant_valid(int prec, int log2n, int v) {
+  switch (v) {
+    case FFT_VARIANT_FUSED_WIDE: return log2n <= kFusedMaxLog2N;
+    case FFT_VARIANT_FUSED_NARROW: return log2n <= kFusedMaxLog2N && fused_has_narrow(prec, log2n);
+    case FFT_VARIANT_CLUSTER: return log2n > kFusedMaxLog2N && cluster_log2k(prec, log2n) >= 0;
+    case FFT_VARIANT_SWEEPS: return log2n > kFusedMaxLog2N;
+  }
+  return false;
+}
+
+int default_variant(int prec, int log2n) {
+  if (log2n <= kFusedMaxLog2N) return FFT_VARIANT_FUSED_WIDE;
+  return cluster_log2k(prec, log2n) >= 0 ? FFT_VARIANT_CLUSTER : FFT_VARIANT_SWEEPS;
+}
+
+// Make the plan run variant v (valid for its size): kernel choice and the
+// kernels' attributes on the current device.
+cudaError_t apply_variant(fft_plan *p, int v) {
+  p->variant = v;
+  p->narrow = v == FFT_VARIANT_FUSED_NARROW;
+  p->kernel = v == FFT_VARIANT_FUSED_WIDE || v == FFT_VARIANT_FUSED_NARROW ? 0 : v == FFT_VARIANT_CLUSTER ? 2 : 1;
+  p->shape = fused_shape(p->prec, p->log2n < kFusedMaxLog2N ? p->log2n : kFusedMaxLog2N, p->narrow);
+  if (p->kernel == 0) return prepare_fused(p->prec, p->log2n, p->narrow);
+  if (p->kernel == 2) return prepare_cluster(p->prec, p->log2n);
+  return prepare_sweeps(p->prec, p->log2n);
+}
+
+// Queue one transform batch of plan p on `stream` (d: 0 forward, 1 inverse).
+cudaError_t plan_launch(const fft_plan *p, const void *in, void *out, int64_t batch, int d, cudaStream_t stream) {
+  const bool scaled = p->scale[d] != 0;
+  if (p->kernel == 0)
+    return launch_fused(p->prec, p->log2n, p->narrow, scaled, in, out, batch, p->twp[d], p->tw0[d], stream);
+  if (p->kernel == 2) return launch_cluster(p->prec, p->log2n, scaled, in, out, nullptr, batch, p->twp[d], stream);
+  return launch_sweeps(p->prec, p->log2n, scaled, in, out, nullptr, batch, p->twp[d], stream);
+}
+
+// ---- autotune cache: a JSON object {"<gpu>|<prec>|<log2n>|<fac>": variant, ...}
+std::mutex g_cache_mu;
+
+std::map<std::string, int> cache_read(const char *path) {
+  std::map<std::string, int> m;
+  FILE *f = fopen(path, "rb");
+  if (!f) return m;
+  std::string text;
+  char buf[4096];
+  size_t k;
+  while ((k = fread(buf, 1, sizeof buf, f)) > 0) text.append(buf, k);
+  fclose(f);
+  size_t i = 0;
+  while ((i = text.find('"', i)) != std::string::npos) {
+    const size_t j = text.find('"', i + 1);
+    if (j == std::string::npos) break;
+    const std::string key = text.substr(i + 1, j - i - 1);
+    size_t c = text.find_first_not_of(" \t\r\n", j + 1);
+    if (c != std::string::npos && text[c] == ':') {
+      c = text.find_first_not_of(" \t\r\n", c + 1);
+      if (c != std::string::npos && (isdigit((unsigned char)text[c]) || text[c] == '-')) m[key] = atoi(text.c_str() + c);
+    }
+    i = j + 1;
+  }
+  return m;
+}
+
+void cache_write(const char *path, const std::map<std::string, int> &m) {
+  const std::string tmp = std::string(path) + ".tmp" + std::to_string((long)getpid());
+  FILE *f = fopen(tmp.c_str(), "wb");
+  if (!f) return;
+  fprintf(f, "{\n  \"format\": 1");
+  for (const auto &kv : m)
+    if (kv.first != "format") fprintf(f, ",\n  \"%s\": %d", kv.first.c_str(), kv.second);
+  fprintf(f, "\n}\n");
+  fclose(f);
+  rename(tmp.c_str(), path);
+}
+
+// Time every valid variant of plan p on a 128 MiB batch and keep the
+// fastest (forward direction).
+cudaError_t autotune_plan(fft_plan *p) {
+  int cands[4], nc = 0;
+  for (int v = FFT_VARIANT_FUSED_WIDE; v <= FFT_VARIANT_SWEEPS; ++v)
+    if (variant_valid(p->prec, p->log2n, v)) cands[nc++] = v;
+  if (nc < 2) return cudaSuccess;
+  cudaDeviceProp prop;
+  cudaError_t e = cudaGetDeviceProperties(&prop, p->device);
+  if (e != cudaSuccess) return e;
+  char key[384];
+  snprintf(key, sizeof key, "%s|%d|%d|%d", prop.name, p->prec, p->log2n, p->fac);
+  const char *path = getenv("DSFFT_AUTOTUNE_CACHE");
+  if (path && *path) {
+    std::lock_guard<std::mutex> lock(g_cache_mu);
+    auto m = cache_read(path);
+    auto it = m.find(key);
+    if (it != m.end() && variant_valid(p->prec, p->log2n, it->second)) {
+      p->autotuned = 2;
+      return apply_variant(p, it->second);
+    }
+  }
+  const size_t eb = p->prec == kFP32 ? 8 : 4;
+  const size_t tbytes = (size_t)p->n * eb;
+  const int64_t batch = std::max<int64_t>(1, (int64_t)((128u << 20) / tbytes));
+  void *in = nullptr, *out = nullptr;
+  cudaStream_t st = nullptr;
+  cudaEvent_t a = nullptr, b = nullptr;
+  int best = -1;
+  float best_ms = 0.f;
+  do {
+    if ((e = cudaMalloc(&in, tbytes * batch)) != cudaSuccess) break;
+    if ((e = cudaMalloc(&out, tbytes * batch)) != cudaSuccess) break;
+    if ((e = cudaMemset(in, 0x11, tbytes * batch)) != cudaSuccess) break;   // finite, normal values
+    if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) break;
+    if ((e = cudaEventCreate(&a)) != cudaSuccess) break;
+    if ((e = cudaEventCreate(&b)) != cudaSuccess) break;
+    for (int c = 0; c < nc && e == cudaSuccess; ++c) {
+      if ((e = apply_variant(p, cands[c])) != cudaSuccess) break;
+      for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = plan_launch(p, in, out, batch, 0, st);
+      if (e != cudaSuccess) break;
+      if ((e = cudaEventRecord(a, st)) != cudaSuccess) break;
+      for (int r = 0; r < 5 && e == cudaSuccess; ++r) e = plan_launch(p, in, out, batch, 0, st);
+      if (e != cudaSuccess) break;
+      if ((e = cudaEventRecord(b, st)) != cudaSuccess) break;
+      if ((e = cudaEventSynchronize(b)) != cudaSuccess) break;
+      float ms = 0.f;
+      if ((e = cudaEventElapsedTime(&ms, a, b)) != cudaSuccess) break;
+      if (best < 0 || ms < best_ms) {
+        best = cands[c];
+        best_ms = ms;
+      }
+    }
+  } while (0);
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  if (st) cudaStreamDestroy(st);
+  if (in) cudaFree(in);
+  if (out) cudaFree(out);
+  if (e != cudaSuccess) return e;
+  p->autotuned = 1;
+  if (path && *path) {
+    std::lock_guard<std::mutex> lock(g_cache_mu);
+    auto m = cache_read(path);
+    m[key] = best;
+    cache_write(path, m);
+  }
+  return apply_variant(p, best);
+}
 
 int ilog2_exact(int64_t n) {
   if (n < 2 || (n & (n - 1)) != 0) return -1;
@@ -188,11 +340,17 @@ fft_status fft_plan_create(fft_plan **plan, int64_t n, fft_precision prec, fft_f
     for (int r : opts.reserved)
       if (r != 0) return FFT_ERR_INVALID_ARG;
   }
+  if (opts.autotune != 0 && opts.autotune != 1) return FFT_ERR_INVALID_ARG;
+  if (opts.variant < FFT_VARIANT_AUTO || opts.variant > FFT_VARIANT_SWEEPS) return FFT_ERR_INVALID_ARG;
   if (!(opts.lf_eps > 0.0) || !(opts.lf_eps < 1.0)) return FFT_ERR_INVALID_ARG;
   for (int s : {opts.scale_forward, opts.scale_inverse})
     if (s != FFT_SCALE_NONE && s != FFT_SCALE_HALF_PER_PASS) return FFT_ERR_INVALID_ARG;
   const int log2n = ilog2_exact(n);
   if (log2n < 1 || log2n > kMaxLog2N) return FFT_ERR_INVALID_SIZE;
+  if (opts.variant != FFT_VARIANT_AUTO && !variant_valid(prec, log2n, opts.variant)) {
+    snprintf(g_last_error, sizeof g_last_error, "variant %d does not exist for N = 2^%d", opts.variant, log2n);
+    return FFT_ERR_UNSUPPORTED;
+  }
 
   DeviceGuard guard(opts.device);
   if (guard.err != cudaSuccess) return cuda_fail(guard.err, "select device");
@@ -209,8 +367,6 @@ fft_status fft_plan_create(fft_plan **plan, int64_t n, fft_precision prec, fft_f
   p->scale[0] = opts.scale_forward;
   p->scale[1] = opts.scale_inverse;
   p->device = device;
-  p->kernel = log2n <= kFusedMaxLog2N ? 0 : cluster_log2k(prec, log2n) >= 0 ? 2 : 1;
-  p->shape = fused_shape(prec, log2n < kFusedMaxLog2N ? log2n : kFusedMaxLog2N);
 
   const size_t entries = (size_t)(n / 2);
   int *counts = nullptr;
@@ -236,9 +392,9 @@ fft_status fft_plan_create(fft_plan **plan, int64_t n, fft_precision prec, fft_f
     if (e != cudaSuccess) { status = cuda_fail(e, "copy stage-0 twiddles"); break; }
     if ((e = cudaMemcpyAsync(host_counts, counts, 2 * sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess) { status = cuda_fail(e, "copy counts"); break; }
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) { status = cuda_fail(e, "table build sync"); break; }
-    e = p->kernel == 0 ? prepare_fused(prec, log2n) : p->kernel == 2 ? prepare_cluster(prec, log2n)
-                                                                      : prepare_sweeps(prec, log2n);
-    if (e != cudaSuccess) { status = cuda_fail(e, "kernel attributes"); break; }
+    const int v = opts.variant != FFT_VARIANT_AUTO ? opts.variant : default_variant(prec, log2n);
+    if ((e = apply_variant(p, v)) != cudaSuccess) { status = cuda_fail(e, "kernel attributes"); break; }
+    if (opts.autotune && opts.variant == FFT_VARIANT_AUTO && (e = autotune_plan(p)) != cudaSuccess) { status = cuda_fail(e, "autotune"); break; }
   } while (0);
   if (st) cudaStreamDestroy(st);
   if (counts) cudaFree(counts);
@@ -284,13 +440,7 @@ fft_status fft_exec(const fft_plan *plan, const void *in, void *out, int64_t bat
   DeviceGuard guard(plan->device);
   if (guard.err != cudaSuccess) return cuda_fail(guard.err, "select device");
   cudaError_t e;
-  const bool scaled = plan->scale[d] != 0;
-  if (plan->kernel == 0)
-    e = launch_fused(plan->prec, plan->log2n, scaled, in, out, batch, plan->twp[d], plan->tw0[d], (cudaStream_t)stream);
-  else if (plan->kernel == 2)
-    e = launch_cluster(plan->prec, plan->log2n, scaled, in, out, nullptr, batch, plan->twp[d], (cudaStream_t)stream);
-  else
-    e = launch_sweeps(plan->prec, plan->log2n, scaled, in, out, nullptr, batch, plan->twp[d], (cudaStream_t)stream);
+  e = plan_launch(plan, in, out, batch, d, (cudaStream_t)stream);
   if (e != cudaSuccess) {
     static const char *what[3] = {"fused kernel launch", "sweep kernel launch", "cluster kernel launch"};
     return cuda_fail(e, what[plan->kernel]);
@@ -327,6 +477,8 @@ fft_status fft_plan_get_info(const fft_plan *plan, fft_plan_info *info) {
   info->scale_inverse = plan->scale[1];
   info->cos_count = plan->cos_count;
   info->sin_count = plan->sin_count;
+  info->variant = plan->variant;
+  info->autotuned = plan->autotuned;
   return FFT_OK;
 }
 

@@ -22,10 +22,10 @@ __global__ void __launch_bounds__(Fused<PREC, LOG2N, LOG2R, SCALED>::TPB, Fused<
 // ---------------------------------------------------------------------------
 // dispatch
 
-template <int PREC, int LOG2N, bool SCALED>
+template <int PREC, int LOG2N, bool NARROW, bool SCALED>
 static cudaError_t launch_one(const void *in, void *out, int64_t batch, const uint4 *tw, const Stage0Twiddles &tw0,
                               cudaStream_t stream) {
-  constexpr int LOG2R = fused_log2r(PREC, LOG2N);
+  constexpr int LOG2R = fused_log2r(PREC, LOG2N, NARROW);
   using K = Fused<PREC, LOG2N, LOG2R, SCALED>;
   using E = typename K::E;
   auto kern = fused_fft_kernel<PREC, LOG2N, LOG2R, SCALED>;
@@ -35,11 +35,11 @@ static cudaError_t launch_one(const void *in, void *out, int64_t batch, const ui
   return cudaGetLastError();
 }
 
-// Raise the dynamic shared-memory limit of both variants on the current
+// Raise the dynamic shared-memory limit of both scalings on the current
 // device (needed above 48 KB); called once per plan creation.
-template <int PREC, int LOG2N>
+template <int PREC, int LOG2N, bool NARROW>
 static cudaError_t prepare_one() {
-  constexpr int LOG2R = fused_log2r(PREC, LOG2N);
+  constexpr int LOG2R = fused_log2r(PREC, LOG2N, NARROW);
   using K = Fused<PREC, LOG2N, LOG2R, false>;
   // Shared-memory carveout: enough for the blocks the register budget lets
   // reside (MINB, at least one), the rest stays L1 for the twiddle table.
@@ -57,9 +57,9 @@ static cudaError_t prepare_one() {
   return cudaSuccess;
 }
 
-template <int PREC, int LOG2N>
+template <int PREC, int LOG2N, bool NARROW>
 static FusedShape shape_one() {
-  constexpr int LOG2R = fused_log2r(PREC, LOG2N);
+  constexpr int LOG2R = fused_log2r(PREC, LOG2N, NARROW);
   using K = Fused<PREC, LOG2N, LOG2R, false>;
   return FusedShape{LOG2R, K::T, K::TPC, K::TPB, K::SMEM};
 }
@@ -69,39 +69,51 @@ using LaunchFn = cudaError_t (*)(const void *, void *, int64_t, const uint4 *, c
 using ShapeFn = FusedShape (*)();
 using PrepareFn = cudaError_t (*)();
 
-template <int PREC, int... L>
+template <int PREC, bool NARROW, int... L>
 struct Table {
-  static constexpr LaunchFn plain[] = {launch_one<PREC, L, false>...};
-  static constexpr LaunchFn scaled[] = {launch_one<PREC, L, true>...};
-  static constexpr ShapeFn shape[] = {shape_one<PREC, L>...};
-  static constexpr PrepareFn prepare[] = {prepare_one<PREC, L>...};
+  static constexpr LaunchFn plain[] = {launch_one<PREC, L, NARROW, false>...};
+  static constexpr LaunchFn scaled[] = {launch_one<PREC, L, NARROW, true>...};
+  static constexpr ShapeFn shape[] = {shape_one<PREC, L, NARROW>...};
+  static constexpr PrepareFn prepare[] = {prepare_one<PREC, L, NARROW>...};
 };
 
 #define DSFFT_LOG2N_LIST 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14
-using T32 = Table<kFP32, DSFFT_LOG2N_LIST>;
-using T16 = Table<kFP16, DSFFT_LOG2N_LIST>;
-using TB16 = Table<kBF16, DSFFT_LOG2N_LIST>;
+template <bool NARROW>
+struct Tables {
+  using T32 = Table<kFP32, NARROW, DSFFT_LOG2N_LIST>;
+  using T16 = Table<kFP16, NARROW, DSFFT_LOG2N_LIST>;
+  using TB16 = Table<kBF16, NARROW, DSFFT_LOG2N_LIST>;
+  static FusedShape shape(int prec, int i) {
+    return prec == kFP32 ? T32::shape[i]() : prec == kFP16 ? T16::shape[i]() : TB16::shape[i]();
+  }
+  static cudaError_t prepare(int prec, int i) {
+    return prec == kFP32 ? T32::prepare[i]() : prec == kFP16 ? T16::prepare[i]() : TB16::prepare[i]();
+  }
+  static LaunchFn launch(int prec, int i, bool scaled) {
+    if (prec == kFP32) return scaled ? T32::scaled[i] : T32::plain[i];
+    if (prec == kFP16) return scaled ? T16::scaled[i] : T16::plain[i];
+    return scaled ? TB16::scaled[i] : TB16::plain[i];
+  }
+};
 
-FusedShape fused_shape(int prec, int log2n) {
+FusedShape fused_shape(int prec, int log2n, bool narrow) {
   if (log2n < 1 || log2n > kFusedMaxLog2N) return FusedShape{0, 0, 0, 0, 0};
-  const int i = log2n - 1;
-  return prec == kFP32 ? T32::shape[i]() : prec == kFP16 ? T16::shape[i]() : TB16::shape[i]();
+  return narrow ? Tables<true>::shape(prec, log2n - 1) : Tables<false>::shape(prec, log2n - 1);
 }
 
-cudaError_t prepare_fused(int prec, int log2n) {
+bool fused_has_narrow(int prec, int log2n) {
+  return log2n >= 1 && log2n <= kFusedMaxLog2N && fused_log2r(prec, log2n, true) != fused_log2r(prec, log2n, false);
+}
+
+cudaError_t prepare_fused(int prec, int log2n, bool narrow) {
   if (log2n < 1 || log2n > kFusedMaxLog2N) return cudaErrorInvalidValue;
-  const int i = log2n - 1;
-  return prec == kFP32 ? T32::prepare[i]() : prec == kFP16 ? T16::prepare[i]() : TB16::prepare[i]();
+  return narrow ? Tables<true>::prepare(prec, log2n - 1) : Tables<false>::prepare(prec, log2n - 1);
 }
 
-cudaError_t launch_fused(int prec, int log2n, bool scaled, const void *in, void *out, int64_t batch,
+cudaError_t launch_fused(int prec, int log2n, bool narrow, bool scaled, const void *in, void *out, int64_t batch,
                          const uint4 *table, const Stage0Twiddles &tw0, cudaStream_t stream) {
   if (log2n < 1 || log2n > kFusedMaxLog2N) return cudaErrorInvalidValue;
-  const int i = log2n - 1;
-  LaunchFn f;
-  if (prec == kFP32) f = scaled ? T32::scaled[i] : T32::plain[i];
-  else if (prec == kFP16) f = scaled ? T16::scaled[i] : T16::plain[i];
-  else f = scaled ? TB16::scaled[i] : TB16::plain[i];
+  LaunchFn f = narrow ? Tables<true>::launch(prec, log2n - 1, scaled) : Tables<false>::launch(prec, log2n - 1, scaled);
   return f(in, out, batch, table, tw0, stream);
 }
 

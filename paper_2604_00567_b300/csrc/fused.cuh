@@ -30,9 +30,12 @@ namespace dsfft {
 
 // Points per thread: 32 four-byte (FP16/BF16) or 16 eight-byte (FP32)
 // elements, so a thread's register block is 32 registers and every exchange
-// is bank-conflict-free with the one-in-32 padding.
-__host__ __device__ constexpr int fused_log2r(int prec, int log2n) {
-  const int r = prec == kFP32 ? 4 : 5;
+// is bank-conflict-free with the one-in-32 padding.  The narrow variant
+// halves the block (twice the threads per transform, more stages); the
+// autotuner picks between them per size.
+__host__ __device__ constexpr int fused_log2r(int prec, int log2n, bool narrow = false) {
+  const int wide = prec == kFP32 ? 4 : 5;
+  const int r = narrow && (log2n - (wide - 1)) <= 10 ? wide - 1 : wide;   // T = N / R <= 1024
   return log2n < r ? log2n : r;
 }
 

@@ -49,9 +49,11 @@ struct FusedShape {
   int threads_per_block;
   int smem_bytes;
 };
-FusedShape fused_shape(int prec, int log2n);
-
-cudaError_t prepare_fused(int prec, int log2n);
+// `narrow`: the half-width register block (see fused_log2r); it exists for a
+// size when fused_has_narrow, otherwise the wide kernel runs.
+FusedShape fused_shape(int prec, int log2n, bool narrow = false);
+bool fused_has_narrow(int prec, int log2n);
+cudaError_t prepare_fused(int prec, int log2n, bool narrow = false);
 
 // Twiddles of the first register stage (passes 0 .. log2(R)-1, whose j is 0
 // for every thread): the first 2^r - 1 per-pass entries, passed by value so
@@ -62,7 +64,7 @@ struct Stage0Twiddles {
 
 // Fused on-chip transform of `batch` signals of length 2^log2n.  `twp` is
 // the device per-pass table, `tw0` its first entries.
-cudaError_t launch_fused(int prec, int log2n, bool scaled, const void *in, void *out, int64_t batch,
+cudaError_t launch_fused(int prec, int log2n, bool narrow, bool scaled, const void *in, void *out, int64_t batch,
                          const uint4 *twp, const Stage0Twiddles &tw0, cudaStream_t stream);
 
 // N > 2^14: two sweeps over HBM (passes [0, ceil(m/2)) then the rest).

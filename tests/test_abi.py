@@ -53,6 +53,7 @@ def test_opts_defaults(lib):
     o = dsfft.PlanOpts()
     assert lib.fft_plan_opts_init(1, ctypes.byref(o)) == 0
     assert o.lf_eps == 1e-7 and o.scale_forward == 1 and o.scale_inverse == 0 and o.device == -1
+    assert o.autotune == 0 and o.variant == 0
     assert lib.fft_plan_opts_init(0, ctypes.byref(o)) == 0
     assert o.scale_forward == 0
     assert lib.fft_plan_opts_init(7, ctypes.byref(o)) == 1
@@ -79,6 +80,16 @@ def test_host_side_validation_without_gpu(lib):
     lib.fft_plan_opts_init(0, ctypes.byref(o))
     o.scale_forward = 3
     assert lib.fft_plan_create(ctypes.byref(h), 1024, 0, 2, ctypes.byref(o)) == 1
+    lib.fft_plan_opts_init(0, ctypes.byref(o))
+    o.variant = 9
+    assert lib.fft_plan_create(ctypes.byref(h), 1024, 0, 2, ctypes.byref(o)) == 1
+    o.variant = 0
+    o.autotune = 2
+    assert lib.fft_plan_create(ctypes.byref(h), 1024, 0, 2, ctypes.byref(o)) == 1
+    o.autotune = 0
+    for n, variant in ((1024, 3), (1024, 4), (1 << 20, 1), (1 << 20, 2), (1 << 18, 3), (1 << 17, 3), (8, 2)):
+        o.variant = variant   # a variant the size does not have (FP32)
+        assert lib.fft_plan_create(ctypes.byref(h), n, 0, 2, ctypes.byref(o)) == 3, (n, variant)
     assert lib.fft_exec(None, None, None, 1, -1, None) == 1
     assert lib.fft_plan_destroy(None) == 0
     assert lib.fft_plan_get_info(None, None) == 1
