@@ -250,13 +250,16 @@ def run_ours(args):
             "batch": batch_for(l), "ms_per_launch": round(ms, 4),
             "transforms_per_s": batch_for(l) / (ms / 1e3), "GB_per_s": round(gbs, 1),
             "frac_of_hbm": round(gbs / hbm_peak, 4), "launches": plans[l].info()["launches"],
+            "variant": plans[l].info()["variant_name"],
             "rel_l2_vs_fp64": error_vs_fp64(plans[l], xs[l], ys[l], l, PRECISION, plans[l].scale_forward),
         }
         if dominant is None or ms > dominant[1]:
             dominant = (l, ms, nbytes, gbs)
     l, ms, nbytes, gbs = dominant
-    kname = (f"fused_fft_kernel fp16 N=2^{l}" if plans[l].info()["kernel"] == 0
-             else f"sweep_fft_kernel x2 fp16 N=2^{l} (one fft_exec)")
+    info_l = plans[l].info()
+    kname = {0: f"fused_fft_kernel fp16 N=2^{l} ({info_l['variant_name']}, R={info_l['points_per_thread']})",
+             1: f"sweep_fft_kernel x2 fp16 N=2^{l} (one fft_exec)",
+             2: f"cluster_fft_kernel fp16 N=2^{l}"}[info_l["kernel"]]
     roofline = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
                 "frac": round(gbs / hbm_peak, 4), "traffic": recorded_traffic(f"fp16_n{1 << l}", nbytes),
                 "kernel": kname, "peak_kind": peak_kind, "algorithmic_bytes_per_launch": nbytes}

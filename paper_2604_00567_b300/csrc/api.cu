@@ -77,8 +77,15 @@ bool variant_valid(int prec, int log2n, int v) {
   return false;
 }
 
+// Built-in choice: the variant the autotuner measured fastest on a B300 for
+// each size (128 MiB batches; opts.autotune re-measures on the running GPU).
 int default_variant(int prec, int log2n) {
-  if (log2n <= kFusedMaxLog2N) return FFT_VARIANT_FUSED_WIDE;
+  if (log2n <= kFusedMaxLog2N) {
+    const bool narrow = prec == kFP32 ? (log2n >= 5 && log2n <= 7)
+                                      : ((log2n >= 5 && log2n <= 8) || log2n == 11 || log2n == 12);
+    return narrow && fused_has_narrow(prec, log2n) ? FFT_VARIANT_FUSED_NARROW : FFT_VARIANT_FUSED_WIDE;
+  }
+  if (log2n == 16) return FFT_VARIANT_SWEEPS;
   return cluster_log2k(prec, log2n) >= 0 ? FFT_VARIANT_CLUSTER : FFT_VARIANT_SWEEPS;
 }
 

@@ -19,10 +19,11 @@ def dsfft():
 
 
 def _expected_kernel(prec, log2n):
-    """Cluster (DSMEM) kernel for FP16/BF16 2^15..2^17 and FP32 2^15..2^16,
-    two HBM sweeps above."""
-    limit = 16 if prec == "fp32" else 17
-    return 2 if log2n <= limit else 1
+    """Built-in choice (measured on B300): the cluster (DSMEM) kernel for
+    2^15 and, for FP16/BF16, 2^17; two HBM sweeps for 2^16 and above."""
+    if log2n == 15 or (log2n == 17 and prec != "fp32"):
+        return 2
+    return 1
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp16", "bf16"])
@@ -42,7 +43,7 @@ def test_large_bitexact(dsfft, prec, log2n):
 def test_cluster_in_place(dsfft, prec, log2n):
     N = 1 << log2n
     x = signals.signal(860 + log2n, 5, N, prec)
-    plan = dsfft.Plan(N, prec, "dual_select")
+    plan = dsfft.Plan(N, prec, "dual_select", variant="cluster")
     assert plan.info()["kernel"] == 2
     assert_bitexact(gpu_fft(plan, x, inplace=True), gpu_fft(plan, x), f"in-place N=2^{log2n} {prec}")
 
