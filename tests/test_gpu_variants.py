@@ -27,7 +27,7 @@ def test_fused_narrow_bitexact(dsfft, prec, log2n):
     plan = dsfft.Plan(N, prec, "dual_select", variant="fused_narrow")
     info = plan.info()
     assert info["variant_name"] == "fused_narrow"
-    wide = dsfft.Plan(N, prec, "dual_select").info()["points_per_thread"]
+    wide = dsfft.Plan(N, prec, "dual_select", variant="fused_wide").info()["points_per_thread"]
     assert info["points_per_thread"] == wide // 2
     for d in (-1, 1):
         assert_bitexact(gpu_fft(plan, x, d), emulate(plan, x, d), f"narrow N=2^{log2n} {prec} dir={d}")
