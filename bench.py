@@ -395,14 +395,15 @@ def run_exec_only(args):
     n = 1 << l
     eb = 8 if prec == "fp32" else 4
     batch = max(1, (args.batch_mib << 20) // (eb * n))
-    plan = dsfft.Plan(n, prec, args.factorization)
+    plan = dsfft.Plan(n, prec, args.factorization, variant=args.variant)
     x = signals.device_signal(batch, n, prec, seed=l)
     y = torch.empty_like(x)
     for _ in range(args.iters):
         plan.exec(x, out=y)
     torch.cuda.synchronize()
     print(json.dumps({"exec_only": True, "N": n, "precision": prec, "batch": batch, "iters": args.iters,
-                      "kernel": plan.info()["kernel"], "launches_per_exec": plan.info()["launches"]}))
+                      "kernel": plan.info()["kernel"], "variant": plan.info()["variant_name"],
+                      "launches_per_exec": plan.info()["launches"]}))
 
 
 def main():
@@ -419,6 +420,8 @@ def main():
     ap.add_argument("--factorization", default="dual_select",
                     choices=["dual_select", "linzer_feig_clamped", "cosine"])
     ap.add_argument("--batch-mib", type=int, default=256)
+    ap.add_argument("--variant", default="auto",
+                    choices=["auto", "fused_wide", "fused_narrow", "cluster", "sweeps"])
     ap.add_argument("--iters", type=int, default=2)
     args = ap.parse_args()
     if args.exec_only is not None:
