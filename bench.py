@@ -16,6 +16,9 @@ Also reported on the same JSON line:
   e2e          : the same metric with the input copied from pinned host
                  memory and the output copied back inside the timed region;
   cpu_baseline : the CPU oracle (op-by-op emulation) on a bounded sample;
+  serve        : the serving loop under a Poisson arrival trace (20k req/s,
+                 mixed N 2^8..2^18, FP32/FP16, 40 GB arena): p50/p99 latency
+                 and throughput;
   clocks       : nvidia-smi samples taken during the timed region.
 
 ``--impl reference`` times the CPU oracle itself on the same workload (a
@@ -307,6 +310,10 @@ def run_ours(args):
            "h2d_bytes_per_step": step_bytes, "d2h_bytes_per_step": step_bytes, "ms_per_step": round(e2e_ms, 3),
            "steps": e2e_steps}
 
+    serve = None
+    if not args.no_serve:
+        serve = serve_measure(args.serve_seconds)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(log2ns, samples_div=CPU_SAMPLE_DIV)
@@ -323,12 +330,81 @@ def run_ours(args):
                        "l2": "inputs 1 GiB per launch > 126 MB L2; no flush", "parallelism": f"replicas{world}"},
             "roofline": roofline, "per_n": per_n, "fp32_plain": fp32, "e2e": e2e,
             "gpu_launches": K * sum(plans[l].info()["launches"] for l in log2ns),
-            "clocks": clocks, "cpu_baseline": cpu,
+            "clocks": clocks, "cpu_baseline": cpu, "serve": serve,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+def serve_trace(seconds: float, rate: float, seed: int = 2):
+    """Open-loop arrival trace: Poisson arrivals at ``rate`` req/s for
+    ``seconds``; each request has U{1..256} signals of N = 2^e, e ~ U{8..18},
+    precision FP32 or FP16 with probability 1/2 (seeded)."""
+    rng = np.random.default_rng(seed)
+    count = int(seconds * rate)
+    arrivals = np.cumsum(rng.exponential(1e9 / rate, count)).astype(np.int64)
+    log2n = rng.integers(8, 19, count)
+    signals_ = rng.integers(1, 257, count)
+    fp32 = rng.random(count) < 0.5
+    return arrivals, log2n, signals_, fp32
+
+
+def serve_measure(seconds: float = 1.0, rate: float = 20000.0, budget: int = 40_000_000_000):
+    """Serving loop under the arrival trace: inputs resident on the device
+    (read from per-precision pools), outputs in the server's 40 GB arena
+    (freed at completion).  Latency = completion seen by the scheduler -
+    submission, per request."""
+    import torch
+    import paper_2604_00567_b300 as dsfft
+    from paper_2604_00567_b300 import signals
+    arrivals, log2n, sig, fp32 = serve_trace(seconds, rate)
+    pools = {"fp32": signals.device_signal(256, 1 << 18, "fp32", seed=21),
+             "fp16": signals.device_signal(256, 1 << 18, "fp16", seed=22)}
+    torch.cuda.synchronize()
+    srv = dsfft.Server(memory_budget=budget, release_on_complete=True)
+    try:
+        reqs = []
+        for k in range(len(arrivals)):
+            prec = "fp32" if fp32[k] else "fp16"
+            n = 1 << int(log2n[k])
+            srv.prepare(n, prec)
+            r = dsfft.Server.request(pools[prec], n, prec, tag=k)
+            r.count = int(sig[k])
+            reqs.append(r)
+        srv.replay(reqs, arrivals, keep=pools)
+        srv.drain(600.0)
+        done = []
+        while True:
+            got = srv.poll(65536)
+            if not got:
+                break
+            done += got
+        st = srv.stats()
+    finally:
+        srv.close()
+    ok = [c for c in done if c["status"] == 0]
+    lat_ms = np.array([(c["t_done_ns"] - c["t_submit_ns"]) / 1e6 for c in ok])
+    t0 = min(c["t_submit_ns"] for c in done)
+    t1 = max(c["t_done_ns"] for c in done)
+    span = (t1 - t0) / 1e9
+    transforms = int(sum(int(sig[c["tag"]]) for c in ok))
+    payload = int(sum(2 * c["bytes"] for c in ok))
+    return {
+        "config": "C5: Poisson %.0f req/s for %.1f s (seed 2), U{1..256} signals, N = 2^U{8..18}, "
+                  "FP32/FP16 p=0.5 (dual_select), inputs resident on the device, 40 GB arena, "
+                  "outputs freed at completion" % (rate, seconds),
+        "requests": len(arrivals), "completed_ok": len(ok),
+        "p50_ms": round(float(np.percentile(lat_ms, 50)), 3), "p99_ms": round(float(np.percentile(lat_ms, 99)), 3),
+        "max_ms": round(float(lat_ms.max()), 3), "mean_ms": round(float(lat_ms.mean()), 3),
+        "requests_per_s": len(ok) / span, "transforms_per_s": transforms / span,
+        "algorithmic_GB_per_s": round(payload / span / 1e9, 1),
+        "ticks": st["ticks"], "requests_per_tick": round(len(ok) / max(1, st["ticks"]), 2),
+        "arena_peak_GB": round(st["arena_peak"] / 1e9, 3), "plans": st["plans"],
+        "wall_s": round(span, 3),
+    }
 
 
 # ---------------------------------------------------------------------------
@@ -414,6 +490,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--log2n", type=int, nargs="+", default=list(LOG2NS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop measurement")
+    ap.add_argument("--serve-seconds", type=float, default=1.0)
+    ap.add_argument("--serve-only", action="store_true", help="print only the serving-loop measurement")
     ap.add_argument("--exec-only", type=int, metavar="LOG2N",
                     help="profiling driver: run --iters transforms of one size and exit")
     ap.add_argument("--precision", default="fp16", choices=["fp32", "fp16", "bf16"])
@@ -426,6 +505,9 @@ def main():
     args = ap.parse_args()
     if args.exec_only is not None:
         run_exec_only(args)
+        return
+    if args.serve_only:
+        print(json.dumps({"serve": serve_measure(args.serve_seconds)}), flush=True)
         return
     if args.impl == "reference":
         run_reference(args)

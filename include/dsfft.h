@@ -281,6 +281,111 @@ typedef struct fft_noalloc_item {
 
 DSFFT_API fft_status fft_exec_batch_noalloc(const fft_noalloc_item *items, int64_t count, void *stream);
 
+/* ---- Serving loop with continuous batching --------------------------------
+ * The paper has no serving layer: this is a front end that keeps requests of
+ * mixed size, precision and direction flowing through the same kernels
+ * (every transform is bit-identical to fft_exec of its request alone).
+ *
+ * A server owns one device arena of `memory_budget` bytes (allocated once at
+ * create), its resident plans (created on first use of a size, or by
+ * fft_server_prepare) and a scheduler thread.  Life of a request:
+ *   submit  -> queued (FIFO);
+ *   admitted when its output (count * n elements) fits in the arena: the
+ *            output slot is taken; a later request never overtakes an
+ *            earlier one that does not fit yet;
+ *   launched in the next "tick": all admitted requests are launched together
+ *            (one persistent launch for every N <= 2^14 transform of the
+ *            tick, one launch per larger request) on one of the server's
+ *            streams, as soon as one of `max_ticks_in_flight` slots is free,
+ *            so arrivals join the GPU's queue while earlier ticks run;
+ *   done     when the tick's event has completed (steady-clock timestamps of
+ *            every step are kept);
+ *   released by fft_server_release (or at completion with
+ *            release_on_complete), which frees the arena slot.
+ * Inputs stay in the caller's device memory and must remain valid and
+ * unmodified until the request is done. */
+typedef struct fft_server fft_server;
+
+typedef struct fft_server_opts {
+    int32_t device;               /* -1: the current device */
+    int32_t max_ticks_in_flight;  /* 1..8 (default 2) */
+    uint64_t memory_budget;       /* arena bytes (default 40e9) */
+    int64_t max_tick_transforms;  /* N <= 2^14 transforms per tick (default 2^20) */
+    int32_t autotune;             /* plans created with autotune (0/1) */
+    int32_t release_on_complete;  /* free the output slot at completion: the
+                                     output pointer is then not usable (0/1) */
+    int32_t reserved[4];          /* must be zero */
+} fft_server_opts;
+
+typedef struct fft_request {
+    int64_t n;                    /* power of two in [2, 2^24] */
+    int32_t precision;            /* fft_precision */
+    int32_t factorization;        /* fft_factorization */
+    int32_t direction;            /* fft_direction */
+    int32_t reserved;             /* must be zero */
+    int64_t count;                /* signals, >= 1 */
+    const void *in;               /* device, count * n elements (fft_exec layout) */
+    uint64_t tag;                 /* returned with the completion */
+} fft_request;
+
+typedef struct fft_completion {
+    uint64_t ticket;
+    uint64_t tag;
+    int32_t status;               /* fft_status of the request */
+    int32_t reserved;
+    void *out;                    /* device, in the arena; valid until released */
+    int64_t bytes;                /* count * n * element bytes */
+    int64_t t_submit_ns;          /* steady clock (CLOCK_MONOTONIC), ns */
+    int64_t t_admit_ns;
+    int64_t t_launch_ns;
+    int64_t t_done_ns;            /* when the scheduler saw the tick complete */
+    int64_t tick;
+} fft_completion;
+
+typedef struct fft_server_stats {
+    int64_t submitted, admitted, completed, released;
+    int64_t queued;               /* waiting for admission */
+    int64_t in_flight;            /* admitted, not yet done */
+    int64_t ticks;
+    int64_t transforms;           /* completed transforms */
+    int64_t plans;                /* resident plans */
+    uint64_t arena_bytes, arena_used, arena_peak;
+    int64_t reserved[4];
+} fft_server_stats;
+
+/* Defaults (see the field comments). */
+DSFFT_API fft_status fft_server_opts_init(fft_server_opts *opts);
+/* Allocates the arena and per-slot descriptor buffers, starts the scheduler
+ * thread.  FFT_ERR_OOM when the arena cannot be allocated. */
+DSFFT_API fft_status fft_server_create(fft_server **server, const fft_server_opts *opts);
+/* Creates (if needed) the resident plan of (n, precision, factorization). */
+DSFFT_API fft_status fft_server_prepare(fft_server *server, int64_t n, fft_precision precision,
+                                        fft_factorization factorization);
+/* Queues a request (thread-safe; never waits for the GPU).  FFT_ERR_OOM when
+ * its output alone exceeds the arena; FFT_ERR_INVALID_SIZE for a bad n or an
+ * N <= 2^14 request of more than max_tick_transforms signals. */
+DSFFT_API fft_status fft_server_submit(fft_server *server, const fft_request *req, uint64_t *ticket);
+/* Submits reqs[i] at start + arrival_ns[i] (open-loop replay of an arrival
+ * trace from the calling thread, which it blocks until the last submission);
+ * tickets[i] receives the ticket (may be null). */
+DSFFT_API fft_status fft_server_replay(fft_server *server, const fft_request *reqs, const int64_t *arrival_ns,
+                                       int64_t count, uint64_t *tickets);
+/* Copies up to `max` completions not yet returned (in completion order). */
+DSFFT_API fft_status fft_server_poll(fft_server *server, fft_completion *out, int64_t max, int64_t *got);
+/* Waits for one ticket; FFT_ERR_TIMEOUT after timeout_s seconds. */
+DSFFT_API fft_status fft_server_wait(fft_server *server, uint64_t ticket, double timeout_s, fft_completion *out);
+/* Copies a done, unreleased request's output to `dst` (device or host) on
+ * `stream` (asynchronous). */
+DSFFT_API fft_status fft_server_copy_out(fft_server *server, uint64_t ticket, void *dst, int64_t bytes, void *stream);
+/* Frees a done request's arena slot (FFT_ERR_INVALID_ARG if not done). */
+DSFFT_API fft_status fft_server_release(fft_server *server, uint64_t ticket);
+/* Waits until every submitted request is done; FFT_ERR_TIMEOUT otherwise
+ * (for example when unreleased outputs keep the queue from being admitted). */
+DSFFT_API fft_status fft_server_drain(fft_server *server, double timeout_s);
+DSFFT_API fft_status fft_server_get_stats(fft_server *server, fft_server_stats *stats);
+/* Drains (up to 60 s), stops the thread and frees everything. */
+DSFFT_API fft_status fft_server_destroy(fft_server *server);
+
 /* Static description of a status code. */
 DSFFT_API const char *fft_status_string(fft_status status);
 

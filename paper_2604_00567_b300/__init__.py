@@ -84,6 +84,34 @@ class BatchInfo(ctypes.Structure):
                 ("device_bytes", ctypes.c_int64)]
 
 
+class ServerOptsC(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("max_ticks_in_flight", ctypes.c_int32),
+                ("memory_budget", ctypes.c_uint64), ("max_tick_transforms", ctypes.c_int64),
+                ("autotune", ctypes.c_int32), ("release_on_complete", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
+
+
+class RequestC(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("precision", ctypes.c_int32), ("factorization", ctypes.c_int32),
+                ("direction", ctypes.c_int32), ("reserved", ctypes.c_int32), ("count", ctypes.c_int64),
+                ("in_", ctypes.c_void_p), ("tag", ctypes.c_uint64)]
+
+
+class CompletionC(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("tag", ctypes.c_uint64), ("status", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("out", ctypes.c_void_p), ("bytes", ctypes.c_int64),
+                ("t_submit_ns", ctypes.c_int64), ("t_admit_ns", ctypes.c_int64),
+                ("t_launch_ns", ctypes.c_int64), ("t_done_ns", ctypes.c_int64), ("tick", ctypes.c_int64)]
+
+
+class ServerStatsC(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("admitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("released", ctypes.c_int64), ("queued", ctypes.c_int64), ("in_flight", ctypes.c_int64),
+                ("ticks", ctypes.c_int64), ("transforms", ctypes.c_int64), ("plans", ctypes.c_int64),
+                ("arena_bytes", ctypes.c_uint64), ("arena_used", ctypes.c_uint64),
+                ("arena_peak", ctypes.c_uint64), ("reserved", ctypes.c_int64 * 4)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -116,10 +144,27 @@ def lib():
             L.fft_batch_get_info.argtypes = [P, ctypes.POINTER(BatchInfo)]
             L.fft_batch_destroy.argtypes = [P]
             L.fft_exec_batch_noalloc.argtypes = [ctypes.POINTER(NoAllocItemC), i64, P]
+            u64 = ctypes.c_uint64
+            L.fft_server_opts_init.argtypes = [ctypes.POINTER(ServerOptsC)]
+            L.fft_server_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(ServerOptsC)]
+            L.fft_server_prepare.argtypes = [P, i64, i32, i32]
+            L.fft_server_submit.argtypes = [P, ctypes.POINTER(RequestC), ctypes.POINTER(u64)]
+            L.fft_server_replay.argtypes = [P, ctypes.POINTER(RequestC), ctypes.POINTER(i64), i64,
+                                            ctypes.POINTER(u64)]
+            L.fft_server_poll.argtypes = [P, ctypes.POINTER(CompletionC), i64, ctypes.POINTER(i64)]
+            L.fft_server_wait.argtypes = [P, u64, d, ctypes.POINTER(CompletionC)]
+            L.fft_server_copy_out.argtypes = [P, u64, P, i64, P]
+            L.fft_server_release.argtypes = [P, u64]
+            L.fft_server_drain.argtypes = [P, d]
+            L.fft_server_get_stats.argtypes = [P, ctypes.POINTER(ServerStatsC)]
+            L.fft_server_destroy.argtypes = [P]
             for name in ("fft_plan_opts_init", "fft_plan_create", "fft_plan_destroy", "fft_exec",
                          "fft_plan_get_table", "fft_plan_get_info", "fft_twiddle_fp64", "fft_batch_create",
                          "fft_batch_exec", "fft_batch_exec_graph", "fft_batch_get_info", "fft_batch_destroy",
-                         "fft_exec_batch_noalloc"):
+                         "fft_exec_batch_noalloc", "fft_server_opts_init", "fft_server_create",
+                         "fft_server_prepare", "fft_server_submit", "fft_server_replay", "fft_server_poll",
+                         "fft_server_wait", "fft_server_copy_out", "fft_server_release", "fft_server_drain",
+                         "fft_server_get_stats", "fft_server_destroy"):
                 getattr(L, name).restype = i32
             _lib = L
     return _lib
@@ -320,6 +365,124 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def _completion(c: CompletionC) -> dict:
+    return {k: getattr(c, k) for k, _ in CompletionC._fields_ if k != "reserved"}
+
+
+class Server:
+    """The serving loop (``fft_server_*``): requests of any size, precision
+    and direction are queued, admitted under the arena budget and launched
+    together in ticks by the library's scheduler thread.  Inputs are CUDA
+    tensors that must stay alive and unchanged until their request is done
+    (the binding keeps a reference until then); outputs live in the server's
+    arena until :meth:`release`."""
+
+    def __init__(self, memory_budget: int = 40_000_000_000, max_ticks_in_flight: int = 2,
+                 max_tick_transforms: int = 1 << 20, device: int | None = None, autotune: bool = False,
+                 release_on_complete: bool = False):
+        L = lib()
+        o = ServerOptsC()
+        _check(L.fft_server_opts_init(ctypes.byref(o)), "fft_server_opts_init")
+        o.memory_budget = int(memory_budget)
+        o.max_ticks_in_flight = int(max_ticks_in_flight)
+        o.max_tick_transforms = int(max_tick_transforms)
+        o.autotune = 1 if autotune else 0
+        o.release_on_complete = 1 if release_on_complete else 0
+        if device is not None:
+            o.device = int(device)
+        h = ctypes.c_void_p()
+        _check(L.fft_server_create(ctypes.byref(h), ctypes.byref(o)), "fft_server_create")
+        self._h = h
+        self._inputs = {}
+
+    @staticmethod
+    def request(x, n: int, precision: str, factorization: str = "dual_select", direction: int = FORWARD,
+                tag: int = 0) -> RequestC:
+        """Request descriptor for the signals of CUDA tensor ``x``."""
+        eb = 8 if precision == "fp32" else 4
+        count = x.numel() * x.element_size() // (eb * int(n))
+        r = RequestC()
+        r.n, r.precision, r.factorization = int(n), PRECISIONS[precision], FACTORIZATIONS[factorization]
+        r.direction, r.reserved, r.count, r.in_, r.tag = int(direction), 0, int(count), x.data_ptr(), int(tag)
+        return r
+
+    def prepare(self, n: int, precision: str, factorization: str = "dual_select"):
+        _check(lib().fft_server_prepare(self._h, int(n), PRECISIONS[precision], FACTORIZATIONS[factorization]),
+               "fft_server_prepare")
+
+    def submit(self, x, n: int, precision: str, factorization: str = "dual_select", direction: int = FORWARD,
+               tag: int = 0) -> int:
+        if not x.is_cuda or not x.is_contiguous():
+            raise ValueError("x must be a contiguous CUDA tensor")
+        r = self.request(x, n, precision, factorization, direction, tag)
+        t = ctypes.c_uint64()
+        _check(lib().fft_server_submit(self._h, ctypes.byref(r), ctypes.byref(t)), "fft_server_submit")
+        self._inputs[t.value] = x
+        return t.value
+
+    def replay(self, requests, arrival_ns, keep=None):
+        """Open-loop replay: ``requests`` (list of RequestC) submitted at
+        ``arrival_ns`` offsets from now; returns the tickets.  ``keep``:
+        tensors the requests read (kept alive by the caller)."""
+        n = len(requests)
+        arr = (RequestC * max(1, n))(*requests)
+        t = (ctypes.c_int64 * max(1, n))(*[int(a) for a in arrival_ns])
+        tickets = (ctypes.c_uint64 * max(1, n))()
+        _check(lib().fft_server_replay(self._h, arr, t, n, tickets), "fft_server_replay")
+        return list(tickets)[:n]
+
+    def poll(self, max_items: int = 4096) -> list:
+        buf = (CompletionC * max(1, max_items))()
+        got = ctypes.c_int64()
+        _check(lib().fft_server_poll(self._h, buf, int(max_items), ctypes.byref(got)), "fft_server_poll")
+        out = [_completion(buf[i]) for i in range(got.value)]
+        for c in out:
+            self._inputs.pop(c["ticket"], None)
+        return out
+
+    def wait(self, ticket: int, timeout_s: float = 30.0) -> dict:
+        c = CompletionC()
+        _check(lib().fft_server_wait(self._h, int(ticket), float(timeout_s), ctypes.byref(c)), "fft_server_wait")
+        self._inputs.pop(int(ticket), None)
+        return _completion(c)
+
+    def copy_out(self, ticket: int, dst, stream=None):
+        """Copy a done request's output into tensor ``dst`` (CUDA or CPU)."""
+        nbytes = dst.numel() * dst.element_size()
+        _check(lib().fft_server_copy_out(self._h, int(ticket), ctypes.c_void_p(dst.data_ptr()), nbytes,
+                                         _stream_handle(stream)), "fft_server_copy_out")
+        return dst
+
+    def release(self, ticket: int):
+        _check(lib().fft_server_release(self._h, int(ticket)), "fft_server_release")
+
+    def drain(self, timeout_s: float = 60.0):
+        _check(lib().fft_server_drain(self._h, float(timeout_s)), "fft_server_drain")
+
+    def stats(self) -> dict:
+        st = ServerStatsC()
+        _check(lib().fft_server_get_stats(self._h, ctypes.byref(st)), "fft_server_get_stats")
+        return {k: getattr(st, k) for k, _ in ServerStatsC._fields_ if k != "reserved"}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().fft_server_destroy(self._h)
+            self._h = None
+            self._inputs.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def exec_batch_noalloc(items, stream=None):
