@@ -106,7 +106,8 @@ cudaError_t plan_launch(const fft_plan *p, const void *in, void *out, int64_t ba
   const bool scaled = p->scale[d] != 0;
   if (p->kernel == 0)
     return launch_fused(p->prec, p->log2n, p->narrow, scaled, in, out, batch, p->twp[d], p->tw0[d], stream);
-  if (p->kernel == 2) return launch_cluster(p->prec, p->log2n, scaled, in, out, nullptr, batch, p->twp[d], stream);
+  if (p->kernel == 2)
+    return launch_cluster(p->prec, p->log2n, scaled, in, out, nullptr, batch, p->twp[d], p->tw0[d], stream);
   return launch_sweeps(p->prec, p->log2n, scaled, in, out, nullptr, batch, p->twp[d], stream);
 }
 
@@ -240,6 +241,8 @@ bool dsfft::plan_view(const fft_plan *p, PlanView *v) {
   v->scale[1] = p->scale[1];
   v->twp[0] = p->twp[0];
   v->twp[1] = p->twp[1];
+  v->tw0[0] = &p->tw0[0];
+  v->tw0[1] = &p->tw0[1];
   return true;
 }
 
@@ -282,7 +285,7 @@ cudaError_t batch_enqueue(const fft_batch *b, cudaStream_t stream) {
     const bool scaled = p->scale[g.dir] != 0;
     if (p->kernel == 2)
       e = launch_cluster(p->prec, p->log2n, scaled, nullptr, nullptr, b->d_items + g.first, g.count, p->twp[g.dir],
-                         stream);
+                         p->tw0[g.dir], stream);
     else
       e = launch_sweeps(p->prec, p->log2n, scaled, nullptr, nullptr, b->d_items + g.first, g.count, p->twp[g.dir],
                         stream);

@@ -17,11 +17,14 @@
 // pass-by-pass algorithm is executed with its own operands and twiddle, so
 // the output is bit-identical to it; HBM sees one read and one write.
 //
-// Shared layout (both phases): value o of local group lg at
-// lg M + (o ^ (lg mod 32)), M the group length.  Lanes of a warp are
+// Shared layout (both phases): value o of local group lg at lg (M + 1) + o,
+// M the group length (one pad element per group).  Lanes of a warp are
 // consecutive groups: their local accesses (same o) fall in distinct banks,
-// and the phase-2 remote reads (same phase-1 group q, consecutive o = g')
-// cover one contiguous, aligned 32-element block of the owner's memory.
+// every access is a per-thread base plus a compile-time offset, and the
+// phase-2 remote reads (same phase-1 group q, consecutive o = g') cover 32
+// consecutive elements of the owner's memory.  The first register stage of
+// phase 1 (passes 0..4, the same twiddles for every thread) reads its
+// twiddles from the kernel parameters (constant bank).
 #include <cooperative_groups.h>
 
 #include "group.cuh"
@@ -62,12 +65,13 @@ struct Clus {
   static constexpr int M2 = 1 << LS2;
   static constexpr int GC1 = M2 / K;     // phase-1 groups per CTA
   static constexpr int GC2 = M1 / K;     // phase-2 groups per CTA
-  using P1 = GroupPasses<PREC, LS1, SCALED>;
-  using P2 = GroupPasses<PREC, LS2, SCALED>;
+  using P1 = GroupPasses<PREC, LS1, 0, SCALED>;
+  using P2 = GroupPasses<PREC, LS2, LS1, SCALED>;
   static constexpr int R = P1::R;
   static constexpr int TPB = GC1 * P1::T;
-  static constexpr int LOCAL = N / K;
-  static constexpr int SMEM = LOCAL * (int)sizeof(E);
+  static constexpr int S1 = M1 + 1;      // padded group strides
+  static constexpr int S2 = M2 + 1;
+  static constexpr int SMEM = (GC1 * S1 > GC2 * S2 ? GC1 * S1 : GC2 * S2) * (int)sizeof(E);
   static_assert(GC2 * P2::T == TPB, "both phases use the same threads");
   static_assert(GC1 >= 32 && GC2 >= 32, "a warp must span 32 groups");
   static_assert(K <= 8, "portable cluster size");
@@ -76,7 +80,8 @@ struct Clus {
 
 template <int PREC, int LOG2N, int LOG2K, bool SCALED, class IO>
 __global__ void __cluster_dims__(1 << LOG2K, 1, 1) __launch_bounds__(Clus<PREC, LOG2N, LOG2K, SCALED>::TPB, 2)
-    cluster_fft_kernel(const IO io, int64_t batch, const uint4 *__restrict__ twp) {
+    cluster_fft_kernel(const IO io, int64_t batch, const uint4 *__restrict__ twp,
+                       const __grid_constant__ Stage0Twiddles tw0) {
   using K = Clus<PREC, LOG2N, LOG2K, SCALED>;
   using E = typename K::E;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -86,6 +91,7 @@ __global__ void __cluster_dims__(1 << LOG2K, 1, 1) __launch_bounds__(Clus<PREC, 
   const int64_t tr = (int64_t)blockIdx.x / K::K;
   // the grid is exactly batch * K blocks, so every cluster is active
   (void)batch;
+  auto tw0f = [&](int i) { return tw0.e[i]; };
 
   E v[K::R];
   // ---- phase 1: passes [0, LS1) ----
@@ -98,10 +104,10 @@ __global__ void __cluster_dims__(1 << LOG2K, 1, 1) __launch_bounds__(Clus<PREC, 
       constexpr int p = decltype(p_)::value;
       v[p] = cl_ldcs(src + (int64_t)(tid + p * K::P1::T) * K::M2);
     });
-    auto at = [&](int o) { return lg * K::M1 + (o ^ (lg & 31)); };
+    E *grp = sm + lg * K::S1;
     K::P1::template run<true>(
-        v, tid, 0, 0, twp, [&](int idx, E val) { sm[at(idx)] = val; }, [&](int idx) { return sm[at(idx)]; },
-        [] { __syncthreads(); }, [&](int o, E val) { sm[at(o)] = val; });
+        v, tid, 0, twp, tw0f, [&](int idx, E val) { grp[idx] = val; }, [&](int idx) { return grp[idx]; },
+        [] { __syncthreads(); }, [&](int o, E val) { grp[o] = val; });
   }
   cluster.sync();   // Z_LS1 complete in every CTA of the cluster
   // ---- phase 2: passes [LS1, m) ----
@@ -115,23 +121,22 @@ __global__ void __cluster_dims__(1 << LOG2K, 1, 1) __launch_bounds__(Clus<PREC, 
     const int gp = rank * K::GC2 + lg;          // g' in [0, M1)
     // Z_LS1[g' + q M1] is value o = g' of phase-1 group q, held by CTA
     // q / GC1 at local group q mod GC1; with q = tid + p T2 and T2 | GC1 the
-    // owner and the group's base are compile-time for each p
-    const uint32_t local_base = (uint32_t)__cvta_generic_to_shared(sm);
+    // owner and the group's offset are compile-time for each p
+    const uint32_t local_base =
+        (uint32_t)__cvta_generic_to_shared(sm) + (uint32_t)((tid * K::S1 + gp) * (int)sizeof(E));
     uint32_t rbase[K::K];
     static_for<0, K::K>([&](auto r_) { rbase[decltype(r_)::value] = dsmem_map(local_base, decltype(r_)::value); });
     static_for<0, K::R>([&](auto p_) {
       constexpr int p = decltype(p_)::value;
       constexpr int owner = (p * K::P2::T) / K::GC1;
       constexpr int gl0 = (p * K::P2::T) % K::GC1;
-      const int gl = gl0 + tid;
-      const int off = gl * K::M1 + (gp ^ (gl & 31));
-      dsmem_ld(rbase[owner] + off * (uint32_t)sizeof(E), v[p]);
+      dsmem_ld(rbase[owner] + (uint32_t)(gl0 * K::S1 * (int)sizeof(E)), v[p]);
     });
     cluster.sync();   // every remote read done before the buffer is reused
-    auto at = [&](int o) { return lg * K::M2 + (o ^ (lg & 31)); };
+    E *grp = sm + lg * K::S2;
     E *dst = io.dst(tr) + gp;
     K::P2::template run<false>(
-        v, tid, gp, K::LS1, twp, [&](int idx, E val) { sm[at(idx)] = val; }, [&](int idx) { return sm[at(idx)]; },
+        v, tid, gp, twp, tw0f, [&](int idx, E val) { grp[idx] = val; }, [&](int idx) { return grp[idx]; },
         [] { __syncthreads(); }, [&](int o, E val) { cl_stcs(dst + (int64_t)o * K::M1, val); });
   }
 }
@@ -146,17 +151,17 @@ int cluster_log2k(int prec, int log2n) {
 
 template <int PREC, int LOG2N, int LOG2K, bool SCALED>
 static cudaError_t launch_cluster_one(const void *in, void *out, const BatchItem *items, int64_t batch,
-                                      const uint4 *twp, cudaStream_t stream) {
+                                      const uint4 *twp, const Stage0Twiddles &tw0, cudaStream_t stream) {
   using K = Clus<PREC, LOG2N, LOG2K, SCALED>;
   using E = typename K::E;
   const int64_t blocks = batch * K::K;
   if (blocks > 0x7FFFFFFF) return cudaErrorInvalidConfiguration;
   if (items) {
     cluster_fft_kernel<PREC, LOG2N, LOG2K, SCALED, GatherIO<E>><<<(unsigned)blocks, K::TPB, K::SMEM, stream>>>(
-        GatherIO<E>{items}, batch, twp);
+        GatherIO<E>{items}, batch, twp, tw0);
   } else {
     cluster_fft_kernel<PREC, LOG2N, LOG2K, SCALED, ContigIO<E>><<<(unsigned)blocks, K::TPB, K::SMEM, stream>>>(
-        ContigIO<E>{static_cast<const E *>(in), static_cast<E *>(out), K::N}, batch, twp);
+        ContigIO<E>{static_cast<const E *>(in), static_cast<E *>(out), K::N}, batch, twp, tw0);
   }
   return cudaGetLastError();
 }
@@ -194,11 +199,11 @@ cudaError_t prepare_cluster(int prec, int log2n) {
 }
 
 cudaError_t launch_cluster(int prec, int log2n, bool scaled, const void *in, void *out, const BatchItem *items,
-                           int64_t batch, const uint4 *twp, cudaStream_t stream) {
-#define DSFFT_CL(P, L, LK)                                                                    \
-  case P * 100 + L:                                                                           \
-    return scaled ? launch_cluster_one<P, L, LK, true>(in, out, items, batch, twp, stream)   \
-                  : launch_cluster_one<P, L, LK, false>(in, out, items, batch, twp, stream);
+                           int64_t batch, const uint4 *twp, const Stage0Twiddles &tw0, cudaStream_t stream) {
+#define DSFFT_CL(P, L, LK)                                                                                 \
+  case P * 100 + L:                                                                                        \
+    return scaled ? launch_cluster_one<P, L, LK, true>(in, out, items, batch, twp, tw0, stream)   \
+                  : launch_cluster_one<P, L, LK, false>(in, out, items, batch, twp, tw0, stream);
   switch (prec * 100 + log2n) {
     DSFFT_CL(kFP32, 15, 2)
     DSFFT_CL(kFP32, 16, 3)

@@ -1,12 +1,14 @@
 // group.cuh — register-stage execution of LS consecutive radix-2 passes on
-// one "group" of 2^LS values, shared by the sweep and cluster kernels.
+// one "group" of 2^LS values (the two phases of the cluster kernel).
 //
 // Before global pass P0 the Stockham array is Z_P0; the LS passes starting
 // at P0 mix, for each group g, the values Z_P0[g + q S] (q in [0, 2^LS),
 // S = N / 2^LS).  Local pass i at local index j_loc is global pass P0 + i at
 // j = jg + j_loc 2^P0 (jg = g mod 2^P0), whose twiddle is per-pass entry
-// 2^(P0+i) - 1 + j.  A thread keeps R = 2^LOG2R values of its group in
-// registers and runs up to LOG2R passes between exchanges; thread `tid`
+// 2^(P0+i) - 1 + j (P0 is a compile-time constant; indices fit in int for
+// the sizes that use this, N <= 2^17).  A thread keeps R = 2^LOG2R values
+// of its group in registers and runs up to LOG2R passes between exchanges;
+// thread `tid`
 // (of T = 2^LS / R per group) starts with local values tid + p T and ends
 // with local outputs o = tid + c T + bitrev(q) C T.
 #pragma once
@@ -15,7 +17,7 @@
 
 namespace dsfft {
 
-template <int PREC, int LS, bool SCALED>
+template <int PREC, int LS, int P0, bool SCALED>
 struct GroupPasses {
   using E = typename Elem<PREC>::T;
   static constexpr int LOG2R = PREC == kFP32 ? 4 : 5;
@@ -23,9 +25,11 @@ struct GroupPasses {
   static constexpr int M = 1 << LS;
   static constexpr int T = M / R;
 
-  template <int PL, int RHO>
-  static __device__ __forceinline__ void compute(E (&v)[R], int tid, int64_t jg, int P0,
-                                                 const uint4 *__restrict__ twp) {
+  // tw0(i): per-pass entry i for the first register stage when P0 = 0 (the
+  // same for every thread: the constant bank).
+  template <int PL, int RHO, class TW0>
+  static __device__ __forceinline__ void compute(E (&v)[R], int tid, int jg, const uint4 *__restrict__ twp,
+                                                 const TW0 &tw0) {
     constexpr int C = R >> RHO;
     static_for<0, C>([&](auto c_) {
       constexpr int c = decltype(c_)::value;
@@ -33,15 +37,17 @@ struct GroupPasses {
       // C (2^RHO - 1) 16-byte entries ahead would exhaust the registers
       if constexpr (c > 0) asm volatile("" ::: "memory");
       const int gl = tid + c * T;
-      const int64_t jloc = gl & ((1 << PL) - 1);
+      const int jloc = gl & ((1 << PL) - 1);
       static_for<0, RHO>([&](auto i_) {
         constexpr int i = decltype(i_)::value;
         constexpr int half = 1 << (RHO - 1 - i);
-        const int p = P0 + PL + i;                         // global pass
-        const uint4 *tp = twp + ((1LL << p) - 1) + jg + (jloc << P0);
+        constexpr int p = P0 + PL + i;                     // global pass
+        const uint4 *tp = twp + ((1 << p) - 1) + jg + (jloc << P0);
         static_for<0, (1 << i)>([&](auto ql_) {
           constexpr int ql = decltype(ql_)::value;
-          const uint4 e = __ldg(tp + ((int64_t)ql << (PL + P0)));
+          uint4 e;
+          if constexpr (P0 == 0 && PL == 0) e = tw0(((1 << i) - 1) + ql);
+          else e = __ldg(tp + (ql << (PL + P0)));
           constexpr int qtop = bitrev(ql, i) << (RHO - i);
           static_for<0, half>([&](auto qh_) {
             constexpr int q = qtop | decltype(qh_)::value;
@@ -57,9 +63,9 @@ struct GroupPasses {
   // the block between them, out(o, value) receives local output o.  With
   // SYNC_OUT the block synchronises before the outputs (when out() writes
   // the exchange buffer).
-  template <bool SYNC_OUT = false, int S = 0, class XW, class XR, class SYNC, class OUT>
-  static __device__ __forceinline__ void run(E (&v)[R], int tid, int64_t jg, int P0, const uint4 *__restrict__ twp,
-                                             XW &&xw, XR &&xr, SYNC &&sync, OUT &&out) {
+  template <bool SYNC_OUT = false, int S = 0, class TW0, class XW, class XR, class SYNC, class OUT>
+  static __device__ __forceinline__ void run(E (&v)[R], int tid, int jg, const uint4 *__restrict__ twp,
+                                             const TW0 &tw0, XW &&xw, XR &&xr, SYNC &&sync, OUT &&out) {
     constexpr int PL = S * LOG2R;
     constexpr int RHO = (LS - PL) < LOG2R ? (LS - PL) : LOG2R;
     constexpr int C = R >> RHO;
@@ -69,7 +75,7 @@ struct GroupPasses {
         v[p] = xr(tid + p * T);
       });
     }
-    compute<PL, RHO>(v, tid, jg, P0, twp);
+    compute<PL, RHO>(v, tid, jg, twp, tw0);
     if constexpr (PL + RHO == LS) {
       if constexpr (SYNC_OUT && S > 0) sync();
       static_for<0, C>([&](auto c_) {
@@ -91,7 +97,7 @@ struct GroupPasses {
         });
       });
       sync();
-      run<SYNC_OUT, S + 1>(v, tid, jg, P0, twp, xw, xr, sync, out);
+      run<SYNC_OUT, S + 1>(v, tid, jg, twp, tw0, xw, xr, sync, out);
     }
   }
 };

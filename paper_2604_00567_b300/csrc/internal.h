@@ -80,8 +80,9 @@ cudaError_t launch_sweeps(int prec, int log2n, bool scaled, const void *in, void
 // transform between the two halves of the passes.  -1 = not handled.
 int cluster_log2k(int prec, int log2n);
 cudaError_t prepare_cluster(int prec, int log2n);
+// `tw0`: the first per-pass entries (the fused kernel's stage-0 twiddles).
 cudaError_t launch_cluster(int prec, int log2n, bool scaled, const void *in, void *out, const BatchItem *items,
-                           int64_t batch, const uint4 *twp, cudaStream_t stream);
+                           int64_t batch, const uint4 *twp, const Stage0Twiddles &tw0, cudaStream_t stream);
 
 // Read-only view of a plan's launch parameters (for entry points outside
 // api.cu); false for a null plan.
@@ -89,6 +90,7 @@ struct PlanView {
   int device, kernel, prec, log2n;
   int scale[2];
   const uint4 *twp[2];
+  const Stage0Twiddles *tw0[2];   // host copies of the first per-pass entries
 };
 
 bool plan_view(const ::fft_plan *p, PlanView *v);
