@@ -408,6 +408,76 @@ def serve_measure(seconds: float = 1.0, rate: float = 20000.0, budget: int = 40_
 
 
 # ---------------------------------------------------------------------------
+UNIT_ROUNDOFF = {"fp32": 2.0 ** -24, "fp16": 2.0 ** -11, "bf16": 2.0 ** -8}
+STUDY_FACS = (("dual_select", 1e-7), ("linzer_feig_clamped", 1e-7), ("linzer_feig_clamped", 2.0 ** -14),
+              ("cosine", 1e-7))
+
+
+def error_study(log2ns=(10, 12, 14, 16, 18, 20, 22, 24), precisions=("fp32", "fp16", "bf16"),
+                dists=("uniform", "gaussian")):
+    """Measured error of the three factorizations (LF also with eps = 2^-14)
+    on the GPU path against numpy's FP64 FFT of the same rounded inputs, next
+    to the cumulative bound of Eq. 11, (1 + |t|max eps)^m - 1, with |t|max of
+    the plan's own rounded table.  FP16/BF16 run with x0.5 per pass (DFT/N),
+    FP32 unscaled.  Per case: a few sampled signals (fewer at large N, where
+    numpy's FFT dominates the time)."""
+    import torch
+    import paper_2604_00567_b300 as dsfft
+    from paper_2604_00567_b300 import signals
+    rows = []
+    for l in log2ns:
+        n = 1 << l
+        count = 4 if l <= 20 else 2 if l <= 22 else 1
+        for prec in precisions:
+            for fac, eps in STUDY_FACS:
+                plan = dsfft.Plan(n, prec, fac, lf_eps=eps)
+                t, m, path = plan.table(-1)
+                finite_t = np.isfinite(t) & np.isfinite(m)
+                tmax = float(np.max(np.abs(t))) if np.all(finite_t) else float("inf")
+                with np.errstate(over="ignore"):
+                    bound = float(np.power(1.0 + tmax * UNIT_ROUNDOFF[prec], float(l)) - 1.0)
+                row = {"N": n, "precision": prec, "factorization": fac, "lf_eps": eps if fac == "linzer_feig_clamped" else None,
+                       "t_max": tmax, "nonfinite_table_entries": int((~finite_t).sum()),
+                       "bound_eq11": bound}
+                for dist in dists:
+                    x = signals.device_signal(count, n, prec, seed=7 * l + 1, dist=dist)
+                    y = plan.exec(x)
+                    torch.cuda.synchronize()
+                    xs, ys = signals.from_torch(x, prec), signals.from_torch(y, prec)
+                    ref = np.fft.fft(xs, axis=-1) / (n if plan.scale_forward else 1)
+                    bad = ~np.isfinite(ys)
+                    row[f"nonfinite_out_{dist}"] = int(bad.sum())
+                    row[f"rel_l2_{dist}"] = (float(np.linalg.norm((ys - ref).ravel()) / np.linalg.norm(ref.ravel()))
+                                             if not bad.any() else float("nan"))
+                    del x, y
+                rows.append(row)
+                plan.close()
+        torch.cuda.empty_cache()
+    return rows
+
+
+def error_study_markdown(rows) -> str:
+    def f(v):
+        if v is None:
+            return "—"
+        if isinstance(v, float):
+            if v != v:
+                return "non-finite"
+            if v == float("inf"):
+                return "inf"
+            return f"{v:.3g}"
+        return str(v)
+    out = ["| N | prec | factorization | \\|t\\|max | Eq. 11 bound | rel L2 uniform | rel L2 gaussian | non-finite outputs |",
+           "|---|---|---|---|---|---|---|---|"]
+    for r in rows:
+        fac = r["factorization"] + (f" (eps={r['lf_eps']:.3g})" if r["lf_eps"] is not None else "")
+        nf = r["nonfinite_out_uniform"] + r["nonfinite_out_gaussian"]
+        out.append(f"| 2^{int(np.log2(r['N']))} | {r['precision']} | {fac} | {f(r['t_max'])} | {f(r['bound_eq11'])} | "
+                   f"{f(r['rel_l2_uniform'])} | {f(r['rel_l2_gaussian'])} | {nf} |")
+    return "\n".join(out)
+
+
+# ---------------------------------------------------------------------------
 def cpu_baseline(log2ns, samples_div=CPU_SAMPLE_DIV, seconds_cap=None):
     """Time the CPU oracle (op-by-op FP16 emulation of the same FFT) on a
     bounded sample of each N's batch, on all host cores."""
@@ -493,6 +563,8 @@ def main():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop measurement")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--serve-only", action="store_true", help="print only the serving-loop measurement")
+    ap.add_argument("--error-study", action="store_true",
+                    help="LF / cosine / dual-select error study across N and precisions (JSON + markdown)")
     ap.add_argument("--exec-only", type=int, metavar="LOG2N",
                     help="profiling driver: run --iters transforms of one size and exit")
     ap.add_argument("--precision", default="fp16", choices=["fp32", "fp16", "bf16"])
@@ -505,6 +577,11 @@ def main():
     args = ap.parse_args()
     if args.exec_only is not None:
         run_exec_only(args)
+        return
+    if args.error_study:
+        rows = error_study()
+        print(error_study_markdown(rows), flush=True)
+        print(json.dumps({"error_study": rows}), flush=True)
         return
     if args.serve_only:
         print(json.dumps({"serve": serve_measure(args.serve_seconds)}), flush=True)
