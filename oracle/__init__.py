@@ -63,6 +63,8 @@ def _load():
             lib.orc_dft_bin.argtypes = [i64, P, i64, i32, P]
             lib.orc_fft_fp64.argtypes = [i64, P, P, i64, i32]
             lib.orc_table.argtypes = [i64, i32, d, i32, i32, i32, P, P, P]
+            lib.orc_table_range.argtypes = [i64, i64, i32, d, i32, i32, d, P, P, P]
+            lib.orc_emulate_fft_r4.argtypes = [i64, i32, i32, i32, P, P, P, d, d, i32, P, P, i64]
             lib.orc_butterfly.argtypes = [i32, i32, d, d, i32, P, P, P, P]
             lib.orc_emulate_fft.argtypes = [i64, i32, i32, P, P, P, P, P, i64]
             lib.orc_round_array.argtypes = [P, P, i64, i32]
@@ -159,6 +161,23 @@ def table(N: int, fac: int, fmt: int, direction: int = -1, scaled: bool = False,
     return t, m, p
 
 
+def table_range(N: int, count: int, fac: int, fmt: int, direction: int = -1, mscale: float = 1.0,
+                eps: float = 1e-7):
+    """The rules of :func:`table` for k in [0, count) (k may exceed N/2),
+    multiplier times ``mscale`` (a power of two) before the rounding."""
+    t = np.empty(count, dtype=np.float64)
+    m = np.empty(count, dtype=np.float64)
+    p = np.empty(count, dtype=np.int32)
+    _load().orc_table_range(int(N), int(count), int(fac), float(eps), 1 if direction > 0 else -1, int(fmt),
+                            float(mscale), _ptr(t), _ptr(m), _ptr(p))
+    return t, m, p
+
+
+def table4(N: int, fac: int, fmt: int, direction: int = -1, scaled: bool = False, eps: float = 1e-7):
+    """Radix-4 table: k in [0, 3N/4), multipliers RN(m/4) when scaled."""
+    return table_range(N, 3 * N // 4, fac, fmt, direction, 0.25 if scaled else 1.0, eps)
+
+
 def butterfly(fmt: int, scaled: bool, t: float, m: float, path: int, a: complex, b: complex):
     """One 6-FMA butterfly (branched on ``path``) — returns (A, B)."""
     av = np.array([a.real, a.imag], dtype=np.float64)
@@ -192,6 +211,43 @@ def emulate_fft(x, fmt: int, t, m, path, scaled: bool = False, threads: int = 1)
             lib.orc_emulate_fft(N, int(fmt), 1 if scaled else 0, _ptr(t), _ptr(m), _ptr(path),
                                 xs[lo:hi].ctypes.data_as(ctypes.c_void_p),
                                 y[lo:hi].ctypes.data_as(ctypes.c_void_p), hi - lo)
+
+    if threads <= 1 or batch < 2:
+        run(0, batch)
+    else:
+        th = min(threads, batch)
+        cuts = [batch * i // th for i in range(th + 1)]
+        ws = [threading.Thread(target=run, args=(cuts[i], cuts[i + 1])) for i in range(th)]
+        for w in ws:
+            w.start()
+        for w in ws:
+            w.join()
+    return y.reshape(x.shape)
+
+
+def emulate_fft_r4(x, fmt: int, t4, m4, path4, e0, scaled: bool = False, inverse: bool = False,
+                   threads: int = 1) -> np.ndarray:
+    """Op-by-op emulation of the radix-4 dual-select FFT (orc_emulate_fft_r4)
+    on each row of ``x``.  ``t4, m4, path4``: the radix-4 table (k < 3N/4);
+    ``e0 = (t, m, path)``: the radix-2 entry k = 0 (used when log2 N is odd)."""
+    x = _as_c128(x)
+    N = x.shape[-1]
+    batch = x.size // N
+    xs = x.reshape(batch, N)
+    y = np.empty_like(xs)
+    t4 = np.ascontiguousarray(t4, dtype=np.float64)
+    m4 = np.ascontiguousarray(m4, dtype=np.float64)
+    path4 = np.ascontiguousarray(path4, dtype=np.int32)
+    need = max(1, 3 * N // 4)
+    assert t4.shape[0] >= need and m4.shape[0] >= need and path4.shape[0] >= need
+    lib = _load()
+
+    def run(lo, hi):
+        if hi > lo:
+            lib.orc_emulate_fft_r4(N, int(fmt), 1 if scaled else 0, 1 if inverse else 0, _ptr(t4), _ptr(m4),
+                                   _ptr(path4), float(e0[0]), float(e0[1]), int(e0[2]),
+                                   xs[lo:hi].ctypes.data_as(ctypes.c_void_p),
+                                   y[lo:hi].ctypes.data_as(ctypes.c_void_p), hi - lo)
 
     if threads <= 1 or batch < 2:
         run(0, batch)

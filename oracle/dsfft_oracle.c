@@ -29,6 +29,14 @@
  *                    forms of Eqs. 4-9, branching on the table flag as the
  *                    Implementation paragraph of Section III describes, each
  *                    FMA rounded once in the target format.
+ *   orc_table_range— the same table rules for any k in [0, count) (the
+ *                    radix-4 passes need W^k for k < 3N/4).
+ *   orc_emulate_fft_r4 — the radix-4 extension the Discussion proposes
+ *                    (dual-select in radix-4 passes): radix-4 Stockham DIT
+ *                    passes, preceded by one radix-2 pass when log2 N is odd,
+ *                    each of the three twiddle products in the 6-FMA form of
+ *                    its own table entry; the operation sequence is spelled
+ *                    out at orc_emulate_fft_r4.
  *
  * Readings where the paper is silent or misprinted:
  *   - Eq. 4 prints s2 = (w_r/w_i) b_r + b_i; that does not reproduce Eq. 2
@@ -196,9 +204,9 @@ void orc_fft_fp64(int64_t N, const double *x, double *y, int64_t batch, int sign
  * dir > 0 conjugates the twiddles (w_i -> -w_i) after the clamp; scaled
  * stores the multiplier as RN(m/2).  Outputs: t, m as the rounded values in
  * double, path as ORC_PATH_COS / ORC_PATH_SIN. */
-void orc_table(int64_t N, int fac, double eps, int dir, int fmt, int scaled,
-               double *t, double *m, int32_t *path) {
-    for (int64_t k = 0; k < N / 2; k++) {
+void orc_table_range(int64_t N, int64_t count, int fac, double eps, int dir, int fmt, double mscale,
+                     double *t, double *m, int32_t *path) {
+    for (int64_t k = 0; k < count; k++) {
         double th = (-2.0 * M_PI * (double)k) / (double)N;
         double wr = cos(th), wi = sin(th);
         int use_cos;
@@ -214,11 +222,18 @@ void orc_table(int64_t N, int fac, double eps, int dir, int fmt, int scaled,
         double tt, mm;
         if (use_cos) { mm = wr; tt = wi / wr; }
         else         { mm = wi; tt = wr / wi; }
-        if (scaled) mm = mm * 0.5;
+        mm = mm * mscale;     /* a power of two: exact */
         t[k] = orc_round(tt, fmt);
         m[k] = orc_round(mm, fmt);
         path[k] = use_cos ? ORC_PATH_COS : ORC_PATH_SIN;
     }
+}
+
+/* Algorithm 1 (or Eqs. 4-6 / 7-9) for k in [0, N/2); the multiplier is
+ * halved (x0.5 per pass) when `scaled`. */
+void orc_table(int64_t N, int fac, double eps, int dir, int fmt, int scaled,
+               double *t, double *m, int32_t *path) {
+    orc_table_range(N, N / 2, fac, eps, dir, fmt, scaled ? 0.5 : 1.0, t, m, path);
 }
 
 /* One butterfly, in the paper's branched form.  Inputs a, b are values of
@@ -280,6 +295,128 @@ void orc_emulate_fft(int64_t N, int fmt, int scaled,
                     Y[2 * (2 * s * L + j) + 1] = A[1];
                     Y[2 * (2 * s * L + L + j)] = B[0];
                     Y[2 * (2 * s * L + L + j) + 1] = B[1];
+                }
+            }
+            double *tmp = Z; Z = Y; Y = tmp;
+        }
+        memcpy(y + 2 * N * bi, Z, sizeof(double) * 2 * (size_t)N);
+    }
+    free(Z);
+    free(Y);
+}
+
+/* ---------------------------------------------------------------------- */
+/* Radix-4 extension.  The paper's Discussion proposes applying the
+ * dual-select choice to radix-4 passes, each twiddle product taking the form
+ * of its own table entry; it gives no operation order, so this is the
+ * definition the library implements (and this emulation checks):
+ *
+ * Pass with span L (sub-transforms of length L done): for s in [0, N/4L),
+ * j in [0, L), inputs a_q = Z[q N/4 + s L + j] (q = 0..3), table entries
+ * e_q = T4[q j N/(4L)] for W_4L^(q j), outputs
+ *   Y[4 s L + p L + j] = sum_q W_4L^(q j) a_q (-/+ i)^(q p)   (forward -i).
+ * Operations (each one correctly rounded in the format):
+ *   (s1_q, s2_q) = Eq. 7 (cosine entry) or Eq. 4 corrected (sine entry) of
+ *                  b = a_q with the entry's ratio t_q,      q = 1, 2, 3
+ *   mr_q = m_q (cosine) or -m_q (sine): W a_q = (mr_q s1_q, m_q s2_q)
+ *   [scaled: a_0 <- RN(a_0 / 4); the table multipliers are RN(m / 4)]
+ *   b3 = (RN(mr_3 s1_3), RN(m_3 s2_3))
+ *   c0 = (fma( mr_2, s1_2, a0r), fma( m_2, s2_2, a0i))      a0 + W^2j a2
+ *   c1 = (fma(-mr_2, s1_2, a0r), fma(-m_2, s2_2, a0i))      a0 - W^2j a2
+ *   c2 = (fma( mr_1, s1_1, b3r), fma( m_1, s2_1, b3i))      W^j a1 + b3
+ *   d3 = (fma(-mr_1, s1_1, b3r), fma(-m_1, s2_1, b3i))      b3 - W^j a1
+ *   y0 = c0 + c2, y2 = c0 - c2 (componentwise RN sums)
+ *   forward: y1 = c1 + i d3 = (RN(c1r - d3i), RN(c1i + d3r)),
+ *            y3 = c1 - i d3 = (RN(c1r + d3i), RN(c1i - d3r));
+ *   inverse: y1 and y3 exchanged (W_4 = +i).
+ * Passes: spans L = 1, 4, 16, ... when log2 N is even; when it is odd, a
+ * radix-2 pass with span 1 first (the butterfly of orc_emulate_fft with the
+ * radix-2 entry k = 0, W^0), then spans 2, 8, 32, ....  Scaled transforms
+ * therefore divide by 4 per radix-4 pass and 2 in the radix-2 pass: DFT/N. */
+
+/* the pair (s1, s2) of Eq. 7 (cosine) or Eq. 4 with corrected s2 (sine) */
+static void pre_products(int fmt, double t, int path, const double b[2], double *s1, double *s2) {
+    if (path == ORC_PATH_COS) {
+        *s1 = orc_fma(-t, b[1], b[0], fmt);
+        *s2 = orc_fma(t, b[0], b[1], fmt);
+    } else {
+        *s1 = orc_fma(-t, b[0], b[1], fmt);
+        *s2 = orc_fma(t, b[1], b[0], fmt);
+    }
+}
+
+static void butterfly4(int fmt, int scaled, int inverse, const double *t, const double *m, const int32_t *path,
+                       const int64_t k[4], const double *a0, const double *a1, const double *a2, const double *a3,
+                       double y[4][2]) {
+    double s1[4], s2[4], mr[4], mi[4];
+    const double *a[4] = {a0, a1, a2, a3};
+    for (int q = 1; q < 4; q++) {
+        pre_products(fmt, t[k[q]], path[k[q]], a[q], &s1[q], &s2[q]);
+        mi[q] = m[k[q]];
+        mr[q] = path[k[q]] == ORC_PATH_COS ? m[k[q]] : -m[k[q]];
+    }
+    double x0r = a0[0], x0i = a0[1];
+    if (scaled) {
+        x0r = orc_mul(x0r, 0.25, fmt);
+        x0i = orc_mul(x0i, 0.25, fmt);
+    }
+    double b3r = orc_mul(mr[3], s1[3], fmt), b3i = orc_mul(mi[3], s2[3], fmt);
+    double c0r = orc_fma(mr[2], s1[2], x0r, fmt), c0i = orc_fma(mi[2], s2[2], x0i, fmt);
+    double c1r = orc_fma(-mr[2], s1[2], x0r, fmt), c1i = orc_fma(-mi[2], s2[2], x0i, fmt);
+    double c2r = orc_fma(mr[1], s1[1], b3r, fmt), c2i = orc_fma(mi[1], s2[1], b3i, fmt);
+    double d3r = orc_fma(-mr[1], s1[1], b3r, fmt), d3i = orc_fma(-mi[1], s2[1], b3i, fmt);
+    y[0][0] = orc_fma(c2r, 1.0, c0r, fmt);
+    y[0][1] = orc_fma(c2i, 1.0, c0i, fmt);
+    y[2][0] = orc_fma(c2r, -1.0, c0r, fmt);
+    y[2][1] = orc_fma(c2i, -1.0, c0i, fmt);
+    double pr = orc_fma(d3i, -1.0, c1r, fmt), pi = orc_fma(d3r, 1.0, c1i, fmt);   /* c1 + i d3 */
+    double nr = orc_fma(d3i, 1.0, c1r, fmt), ni = orc_fma(d3r, -1.0, c1i, fmt);   /* c1 - i d3 */
+    int f = inverse ? 3 : 1, g = inverse ? 1 : 3;
+    y[f][0] = pr; y[f][1] = pi;
+    y[g][0] = nr; y[g][1] = ni;
+}
+
+/* The radix-4 (+ one radix-2) FFT defined above.  (t4, m4, path4): the
+ * table for k in [0, 3N/4) with multipliers RN(m/4) when scaled (m unscaled
+ * otherwise); (t0, m0, path0): the radix-2 entry k = 0 (multiplier RN(m/2)
+ * when scaled) used by the radix-2 pass of odd log2 N. */
+void orc_emulate_fft_r4(int64_t N, int fmt, int scaled, int inverse,
+                        const double *t4, const double *m4, const int32_t *path4,
+                        double t0, double m0, int32_t path0,
+                        const double *x, double *y, int64_t batch) {
+    double *Z = (double *)malloc(sizeof(double) * 2 * (size_t)N);
+    double *Y = (double *)malloc(sizeof(double) * 2 * (size_t)N);
+    int log2n = 0;
+    while ((int64_t)1 << log2n < N) log2n++;
+    for (int64_t bi = 0; bi < batch; bi++) {
+        memcpy(Z, x + 2 * N * bi, sizeof(double) * 2 * (size_t)N);
+        int64_t L = 1;
+        if (log2n & 1) {
+            /* radix-2 pass, span 1: a = Z[s], b = Z[N/2 + s] -> Y[2s], Y[2s + 1] */
+            for (int64_t s = 0; s < N / 2; s++) {
+                double A[2], B[2];
+                butterfly(fmt, scaled, t0, m0, path0, &Z[2 * s], &Z[2 * (N / 2 + s)], A, B);
+                Y[2 * (2 * s)] = A[0];
+                Y[2 * (2 * s) + 1] = A[1];
+                Y[2 * (2 * s + 1)] = B[0];
+                Y[2 * (2 * s + 1) + 1] = B[1];
+            }
+            double *tmp = Z; Z = Y; Y = tmp;
+            L = 2;
+        }
+        for (; L < N; L *= 4) {
+            for (int64_t s = 0; s < N / (4 * L); s++) {
+                for (int64_t j = 0; j < L; j++) {
+                    int64_t k1 = j * (N / (4 * L));
+                    int64_t k[4] = {0, k1, 2 * k1, 3 * k1};
+                    double yv[4][2];
+                    butterfly4(fmt, scaled, inverse, t4, m4, path4, k, &Z[2 * (s * L + j)],
+                               &Z[2 * (N / 4 + s * L + j)], &Z[2 * (N / 2 + s * L + j)],
+                               &Z[2 * (3 * N / 4 + s * L + j)], yv);
+                    for (int p = 0; p < 4; p++) {
+                        Y[2 * (4 * s * L + p * L + j)] = yv[p][0];
+                        Y[2 * (4 * s * L + p * L + j) + 1] = yv[p][1];
+                    }
                 }
             }
             double *tmp = Z; Z = Y; Y = tmp;
