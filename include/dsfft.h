@@ -110,7 +110,17 @@ typedef struct fft_plan_opts {
     int32_t autotune;
     int32_t variant;        /* fft_variant; a variant the size does not have
                                gives FFT_ERR_UNSUPPORTED */
-    int32_t reserved[3];    /* must be zero */
+    /* 0 or 2: radix-2 passes (the paper's algorithm).  4: radix-4 passes
+     * (the radix-4 extension the paper's Discussion proposes; N <= 2^14,
+     * fused kernel only, otherwise FFT_ERR_UNSUPPORTED): each radix-4 pass
+     * (span L) maps Z[q N/4 + s L + j], q = 0..3, to
+     * Y[4 s L + p L + j] = sum_q W_4L^(q j) Z[...] (-i)^(q p) (+i inverse);
+     * each of its three twiddle products uses the 6-FMA form of its own
+     * dual-select entry, then four sums; one radix-2 pass (span 1) first when
+     * log2 N is odd.  Scaled directions divide by 4 per radix-4 pass.  The
+     * results differ from the radix-2 algorithm's in rounding only. */
+    int32_t radix;
+    int32_t reserved[2];    /* must be zero */
 } fft_plan_opts;
 
 typedef struct fft_plan_info {
@@ -133,6 +143,8 @@ typedef struct fft_plan_info {
     int32_t sin_count;          /* table entries on the sine path */
     int32_t variant;            /* fft_variant the plan runs */
     int32_t autotuned;          /* 1 = chosen by timing, 2 = from the cache */
+    int32_t radix;              /* 2 or 4 */
+    int32_t reserved;
 } fft_plan_info;
 
 typedef struct fft_plan fft_plan;
@@ -177,6 +189,12 @@ DSFFT_API fft_status fft_exec(const fft_plan *plan, const void *in, void *out, i
  * carries the x0.5 of a scaled direction.  Synchronous. */
 DSFFT_API fft_status fft_plan_get_table(const fft_plan *plan, fft_direction dir, void *host_dst,
                               size_t bytes);
+
+/* Radix-4 plans: copy the packed radix-4 table of `dir` (3N/4 entries of
+ * 16 bytes, k in [0, 3N/4): W^k by the rules above, multipliers divided by 4
+ * on a scaled direction; same entry layout as fft_plan_get_table) to host
+ * memory.  FFT_ERR_UNSUPPORTED for a radix-2 plan. */
+DSFFT_API fft_status fft_plan_get_table4(const fft_plan *plan, fft_direction dir, void *host_dst, size_t bytes);
 
 /* Describe the plan (kernel choice, launch shape, table sizes). */
 DSFFT_API fft_status fft_plan_get_info(const fft_plan *plan, fft_plan_info *info);

@@ -49,7 +49,7 @@ class PlanOpts(ctypes.Structure):
     _fields_ = [("lf_eps", ctypes.c_double), ("scale_forward", ctypes.c_int32),
                 ("scale_inverse", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("autotune", ctypes.c_int32), ("variant", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("radix", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -60,7 +60,8 @@ class PlanInfo(ctypes.Structure):
                 ("table_bytes", ctypes.c_int64), ("element_bytes", ctypes.c_int64),
                 ("scale_forward", ctypes.c_int32), ("scale_inverse", ctypes.c_int32),
                 ("cos_count", ctypes.c_int32), ("sin_count", ctypes.c_int32),
-                ("variant", ctypes.c_int32), ("autotuned", ctypes.c_int32)]
+                ("variant", ctypes.c_int32), ("autotuned", ctypes.c_int32), ("radix", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class BatchItemC(ctypes.Structure):
@@ -131,6 +132,7 @@ def lib():
             L.fft_plan_destroy.argtypes = [P]
             L.fft_exec.argtypes = [P, P, P, i64, i32, P]
             L.fft_plan_get_table.argtypes = [P, i32, P, ctypes.c_size_t]
+            L.fft_plan_get_table4.argtypes = [P, i32, P, ctypes.c_size_t]
             L.fft_plan_get_info.argtypes = [P, ctypes.POINTER(PlanInfo)]
             L.fft_twiddle_fp64.argtypes = [i64, i32, d, P, P, P]
             L.fft_status_string.restype = ctypes.c_char_p
@@ -159,7 +161,7 @@ def lib():
             L.fft_server_get_stats.argtypes = [P, ctypes.POINTER(ServerStatsC)]
             L.fft_server_destroy.argtypes = [P]
             for name in ("fft_plan_opts_init", "fft_plan_create", "fft_plan_destroy", "fft_exec",
-                         "fft_plan_get_table", "fft_plan_get_info", "fft_twiddle_fp64", "fft_batch_create",
+                         "fft_plan_get_table", "fft_plan_get_table4", "fft_plan_get_info", "fft_twiddle_fp64", "fft_batch_create",
                          "fft_batch_exec", "fft_batch_exec_graph", "fft_batch_get_info", "fft_batch_destroy",
                          "fft_exec_batch_noalloc", "fft_server_opts_init", "fft_server_create",
                          "fft_server_prepare", "fft_server_submit", "fft_server_replay", "fft_server_poll",
@@ -188,7 +190,7 @@ class Plan:
     def __init__(self, n: int, precision: str = "fp32", factorization: str = "dual_select",
                  lf_eps: float = 1e-7, scale_forward: bool | None = None,
                  scale_inverse: bool | None = None, device: int | None = None,
-                 variant: str = "auto", autotune: bool = False):
+                 variant: str = "auto", autotune: bool = False, radix: int = 2):
         L = lib()
         self.n = int(n)
         self.precision = precision
@@ -204,6 +206,8 @@ class Plan:
             opts.device = int(device)
         opts.variant = VARIANTS[variant]
         opts.autotune = 1 if autotune else 0
+        opts.radix = int(radix)
+        self.radix = int(radix)
         self.scale_forward = bool(opts.scale_forward)
         self.scale_inverse = bool(opts.scale_inverse)
         h = ctypes.c_void_p()
@@ -286,10 +290,25 @@ class Plan:
                                         buf.nbytes), "fft_plan_get_table")
         return buf
 
+    def raw_table4(self, direction: int = FORWARD) -> np.ndarray:
+        """Radix-4 plans: the packed radix-4 table (k < 3N/4) as (3N/4, 4) uint32."""
+        h = 3 * self.n // 4
+        buf = np.empty((max(h, 1), 4), dtype=np.uint32)
+        _check(lib().fft_plan_get_table4(self._h, int(direction), buf.ctypes.data_as(ctypes.c_void_p),
+                                         buf.nbytes), "fft_plan_get_table4")
+        return buf[:h]
+
+    def table4(self, direction: int = FORWARD):
+        """Decode the radix-4 table like :meth:`table` (m includes the /4 of a
+        scaled direction)."""
+        return self._decode(self.raw_table4(direction))
+
     def table(self, direction: int = FORWARD):
         """Decode the packed table: ``(t, m, path)`` as float64/float64/int32
         arrays (m includes the x0.5 of a scaled direction)."""
-        raw = self.raw_table(direction)
+        return self._decode(self.raw_table(direction))
+
+    def _decode(self, raw):
         if self.precision == "fp32":
             path = raw[:, 3].astype(np.int32)
         else:

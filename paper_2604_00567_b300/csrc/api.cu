@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "../../include/dsfft.h"
+#include "fused4.cuh"
 #include "internal.h"
 
 using namespace dsfft;
@@ -35,6 +36,10 @@ struct fft_plan {
   int autotuned;        // 0 built-in, 1 timed, 2 cache
   FusedShape shape;
   int cos_count, sin_count;
+  int radix;            // 2, or 4 (radix-4 passes, fused kernel only)
+  uint4 *table4[2];     // radix-4: packed table, k in [0, 3N/4)
+  uint4 *twp4[2];       // radix-4: per-pass table (N - 1 - log2 N mod 2 entries)
+  Stage0R4 s0r4[2];     // radix-4: first-stage twiddles (host copy)
 };
 
 namespace {
@@ -104,6 +109,8 @@ cudaError_t apply_variant(fft_plan *p, int v) {
 // Queue one transform batch of plan p on `stream` (d: 0 forward, 1 inverse).
 cudaError_t plan_launch(const fft_plan *p, const void *in, void *out, int64_t batch, int d, cudaStream_t stream) {
   const bool scaled = p->scale[d] != 0;
+  if (p->radix == 4)
+    return launch_fused4(p->prec, p->log2n, scaled, d, in, out, batch, p->twp4[d], p->s0r4[d], stream);
   if (p->kernel == 0)
     return launch_fused(p->prec, p->log2n, p->narrow, scaled, in, out, batch, p->twp[d], p->tw0[d], stream);
   if (p->kernel == 2)
@@ -243,6 +250,7 @@ bool dsfft::plan_view(const fft_plan *p, PlanView *v) {
   v->twp[1] = p->twp[1];
   v->tw0[0] = &p->tw0[0];
   v->tw0[1] = &p->tw0[1];
+  v->radix = p->radix;
   return true;
 }
 
@@ -351,12 +359,22 @@ fft_status fft_plan_create(fft_plan **plan, int64_t n, fft_precision prec, fft_f
       if (r != 0) return FFT_ERR_INVALID_ARG;
   }
   if (opts.autotune != 0 && opts.autotune != 1) return FFT_ERR_INVALID_ARG;
+  if (opts.radix != 0 && opts.radix != 2 && opts.radix != 4) return FFT_ERR_INVALID_ARG;
   if (opts.variant < FFT_VARIANT_AUTO || opts.variant > FFT_VARIANT_SWEEPS) return FFT_ERR_INVALID_ARG;
   if (!(opts.lf_eps > 0.0) || !(opts.lf_eps < 1.0)) return FFT_ERR_INVALID_ARG;
   for (int s : {opts.scale_forward, opts.scale_inverse})
     if (s != FFT_SCALE_NONE && s != FFT_SCALE_HALF_PER_PASS) return FFT_ERR_INVALID_ARG;
   const int log2n = ilog2_exact(n);
   if (log2n < 1 || log2n > kMaxLog2N) return FFT_ERR_INVALID_SIZE;
+  const int radix = opts.radix == 4 ? 4 : 2;
+  if (radix == 4 && log2n > kFusedMaxLog2N) {
+    snprintf(g_last_error, sizeof g_last_error, "radix-4 passes are implemented for N <= 2^%d", kFusedMaxLog2N);
+    return FFT_ERR_UNSUPPORTED;
+  }
+  if (radix == 4 && opts.variant != FFT_VARIANT_AUTO && opts.variant != FFT_VARIANT_FUSED_WIDE) {
+    snprintf(g_last_error, sizeof g_last_error, "radix-4 plans run the fused radix-4 kernel only");
+    return FFT_ERR_UNSUPPORTED;
+  }
   if (opts.variant != FFT_VARIANT_AUTO && !variant_valid(prec, log2n, opts.variant)) {
     snprintf(g_last_error, sizeof g_last_error, "variant %d does not exist for N = 2^%d", opts.variant, log2n);
     return FFT_ERR_UNSUPPORTED;
@@ -377,6 +395,7 @@ fft_status fft_plan_create(fft_plan **plan, int64_t n, fft_precision prec, fft_f
   p->scale[0] = opts.scale_forward;
   p->scale[1] = opts.scale_inverse;
   p->device = device;
+  p->radix = radix;
 
   const size_t entries = (size_t)(n / 2);
   int *counts = nullptr;
@@ -391,8 +410,8 @@ fft_status fft_plan_create(fft_plan **plan, int64_t n, fft_precision prec, fft_f
     if ((e = cudaMalloc(&counts, 2 * sizeof(int))) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc counts"); break; }
     if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) { status = cuda_fail(e, "stream"); break; }
     if ((e = cudaMemsetAsync(counts, 0, 2 * sizeof(int), st)) != cudaSuccess) { status = cuda_fail(e, "memset"); break; }
-    if ((e = launch_build_table(log2n, fac, opts.lf_eps, prec, 0, p->scale[0], p->table[0], counts, st)) != cudaSuccess) { status = cuda_fail(e, "table build"); break; }
-    if ((e = launch_build_table(log2n, fac, opts.lf_eps, prec, 1, p->scale[1], p->table[1], nullptr, st)) != cudaSuccess) { status = cuda_fail(e, "table build"); break; }
+    if ((e = launch_build_table(log2n, n / 2, fac, opts.lf_eps, prec, 0, p->scale[0] ? 0.5 : 1.0, p->table[0], counts, st)) != cudaSuccess) { status = cuda_fail(e, "table build"); break; }
+    if ((e = launch_build_table(log2n, n / 2, fac, opts.lf_eps, prec, 1, p->scale[1] ? 0.5 : 1.0, p->table[1], nullptr, st)) != cudaSuccess) { status = cuda_fail(e, "table build"); break; }
     if ((e = launch_per_pass_table(log2n, p->table[0], p->twp[0], st)) != cudaSuccess) { status = cuda_fail(e, "per-pass table"); break; }
     if ((e = launch_per_pass_table(log2n, p->table[1], p->twp[1], st)) != cudaSuccess) { status = cuda_fail(e, "per-pass table"); break; }
     for (int d = 0; d < 2; ++d) {
@@ -401,7 +420,32 @@ fft_status fft_plan_create(fft_plan **plan, int64_t n, fft_precision prec, fft_f
     }
     if (e != cudaSuccess) { status = cuda_fail(e, "copy stage-0 twiddles"); break; }
     if ((e = cudaMemcpyAsync(host_counts, counts, 2 * sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess) { status = cuda_fail(e, "copy counts"); break; }
+    if (radix == 4) {
+      const int64_t c4 = 3 * n / 4, p4 = n - 1 - (log2n & 1);
+      for (int d = 0; d < 2 && e == cudaSuccess; ++d) {
+        if ((e = cudaMalloc(&p->table4[d], (size_t)(c4 > 0 ? c4 : 1) * sizeof(uint4))) != cudaSuccess) break;
+        if ((e = cudaMalloc(&p->twp4[d], (size_t)(p4 > 0 ? p4 : 1) * sizeof(uint4))) != cudaSuccess) break;
+        if ((e = launch_build_table(log2n, c4, fac, opts.lf_eps, prec, d, p->scale[d] ? 0.25 : 1.0, p->table4[d],
+                                    nullptr, st)) != cudaSuccess)
+          break;
+        if ((e = launch_per_pass_table4(log2n, p->table4[d], p->twp4[d], st)) != cudaSuccess) break;
+        memset(&p->s0r4[d], 0, sizeof(Stage0R4));
+        p->s0r4[d].r2 = p->tw0[d].e[0];
+        const int64_t cnt = p4 < 31 ? p4 : 31;
+        if (cnt > 0 && (e = cudaMemcpyAsync(p->s0r4[d].e, p->twp4[d], (size_t)cnt * sizeof(uint4),
+                                            cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+          break;
+      }
+      if (e != cudaSuccess) { status = cuda_fail(e, "radix-4 tables"); break; }
+    }
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) { status = cuda_fail(e, "table build sync"); break; }
+    if (radix == 4) {
+      p->variant = FFT_VARIANT_FUSED_WIDE;
+      p->kernel = 0;
+      p->shape = fused4_shape(prec, log2n);
+      if ((e = prepare_fused4(prec, log2n)) != cudaSuccess) { status = cuda_fail(e, "kernel attributes"); break; }
+      break;
+    }
     const int v = opts.variant != FFT_VARIANT_AUTO ? opts.variant : default_variant(prec, log2n);
     if ((e = apply_variant(p, v)) != cudaSuccess) { status = cuda_fail(e, "kernel attributes"); break; }
     if (opts.autotune && opts.variant == FFT_VARIANT_AUTO && (e = autotune_plan(p)) != cudaSuccess) { status = cuda_fail(e, "autotune"); break; }
@@ -412,6 +456,8 @@ fft_status fft_plan_create(fft_plan **plan, int64_t n, fft_precision prec, fft_f
     for (int d = 0; d < 2; ++d) {
       if (p->table[d]) cudaFree(p->table[d]);
       if (p->twp[d]) cudaFree(p->twp[d]);
+      if (p->table4[d]) cudaFree(p->table4[d]);
+      if (p->twp4[d]) cudaFree(p->twp4[d]);
     }
     delete p;
     return status;
@@ -428,6 +474,8 @@ fft_status fft_plan_destroy(fft_plan *plan) {
   for (int d = 0; d < 2; ++d) {
     if (plan->table[d]) cudaFree(plan->table[d]);
     if (plan->twp[d]) cudaFree(plan->twp[d]);
+    if (plan->table4[d]) cudaFree(plan->table4[d]);
+    if (plan->twp4[d]) cudaFree(plan->twp4[d]);
   }
   delete plan;
   return FFT_OK;
@@ -458,6 +506,19 @@ fft_status fft_exec(const fft_plan *plan, const void *in, void *out, int64_t bat
   return FFT_OK;
 }
 
+fft_status fft_plan_get_table4(const fft_plan *plan, fft_direction dir, void *host_dst, size_t bytes) {
+  if (!plan || !host_dst) return FFT_ERR_INVALID_ARG;
+  if (dir != FFT_FORWARD && dir != FFT_INVERSE) return FFT_ERR_INVALID_ARG;
+  if (plan->radix != 4) return FFT_ERR_UNSUPPORTED;
+  const size_t need = (size_t)(3 * plan->n / 4) * sizeof(uint4);
+  if (bytes < need) return FFT_ERR_INVALID_ARG;
+  if (need == 0) return FFT_OK;
+  DeviceGuard guard(plan->device);
+  cudaError_t e = cudaMemcpy(host_dst, plan->table4[dir == FFT_FORWARD ? 0 : 1], need, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "copy table");
+  return FFT_OK;
+}
+
 fft_status fft_plan_get_table(const fft_plan *plan, fft_direction dir, void *host_dst, size_t bytes) {
   if (!plan || !host_dst) return FFT_ERR_INVALID_ARG;
   if (dir != FFT_FORWARD && dir != FFT_INVERSE) return FFT_ERR_INVALID_ARG;
@@ -482,6 +543,7 @@ fft_status fft_plan_get_info(const fft_plan *plan, fft_plan_info *info) {
   info->threads_per_transform = plan->shape.threads_per_transform;
   info->transforms_per_block = plan->shape.transforms_per_block;
   info->table_bytes = (int64_t)2 * (plan->n / 2 + plan->n - 1) * (int64_t)sizeof(uint4);
+  if (plan->radix == 4) info->table_bytes += (int64_t)2 * (3 * plan->n / 4 + plan->n - 1) * (int64_t)sizeof(uint4);
   info->element_bytes = (int64_t)elem_bytes(plan->prec);
   info->scale_forward = plan->scale[0];
   info->scale_inverse = plan->scale[1];
@@ -489,6 +551,7 @@ fft_status fft_plan_get_info(const fft_plan *plan, fft_plan_info *info) {
   info->sin_count = plan->sin_count;
   info->variant = plan->variant;
   info->autotuned = plan->autotuned;
+  info->radix = plan->radix;
   return FFT_OK;
 }
 

@@ -151,4 +151,80 @@ template <int PREC, bool SCALED> struct BflyPacked {
 template <bool SCALED> struct Bfly<kFP16, SCALED> : BflyPacked<kFP16, SCALED> {};
 template <bool SCALED> struct Bfly<kBF16, SCALED> : BflyPacked<kBF16, SCALED> {};
 
+// ---------------------------------------------------------------------------
+// Radix-4 butterfly (the radix-4 extension of the Discussion: each of the
+// three twiddle products takes the form of its own table entry).  Inputs
+// a0..a3 = Z[q N/4 + s L + j], entries e1..e3 of W_4L^(q j); with
+// (u_q, v_q) the pre-products above and W a_q = (sigma m u, m v):
+//   b3 = W^3j a3 (two rounded multiplies)
+//   c0 = a0 + W^2j a2, c1 = a0 - W^2j a2, c2 = W^j a1 + b3, d3 = b3 - W^j a1
+//   y0 = c0 + c2, y2 = c0 - c2, y1 = c1 + s i d3, y3 = c1 - s i d3,
+// s = +1 forward (y1 = c1 - i c3 with c3 = -d3), -1 inverse, every step one
+// correctly rounded operation (the sums as fma(x, +-1, y), exact products).
+// Scaled: a0 <- RN(a0 / 4) and the table multipliers are RN(m / 4).
+// Outputs go to the registers of two consecutive radix-2 passes' results:
+// a0 <- y0, a1 <- y2, a2 <- y1, a3 <- y3.
+template <int PREC, bool SCALED> struct Bfly4;
+
+template <bool SCALED> struct Bfly4<kFP32, SCALED> {
+  static __device__ __forceinline__ float2 pre(const float2 b, const uint4 e) {
+    const float t = __uint_as_float(e.x);
+    const bool sine = e.w != 0u;
+    const float R = sine ? b.y : b.x;
+    const float S = sine ? b.x : b.y;
+    return make_float2(__fmaf_rn(-t, S, R), __fmaf_rn(t, R, S));
+  }
+  // sgn: -1 forward, +1 inverse (the sign of the real part of y1's d3 term)
+  static __device__ __forceinline__ void run(float2 &a0, float2 &a1, float2 &a2, float2 &a3, const uint4 e1,
+                                             const uint4 e2, const uint4 e3, const float sgn) {
+    const float2 p1 = pre(a1, e1), p2 = pre(a2, e2), p3 = pre(a3, e3);
+    float x0r = a0.x, x0i = a0.y;
+    if (SCALED) {
+      x0r = __fmul_rn(x0r, 0.25f);
+      x0i = __fmul_rn(x0i, 0.25f);
+    }
+    const float m1 = __uint_as_float(e1.y), sm1 = __uint_as_float(e1.z);
+    const float m2 = __uint_as_float(e2.y), sm2 = __uint_as_float(e2.z);
+    const float m3 = __uint_as_float(e3.y), sm3 = __uint_as_float(e3.z);
+    const float b3r = __fmul_rn(sm3, p3.x), b3i = __fmul_rn(m3, p3.y);
+    const float c0r = __fmaf_rn(sm2, p2.x, x0r), c0i = __fmaf_rn(m2, p2.y, x0i);
+    const float c1r = __fmaf_rn(-sm2, p2.x, x0r), c1i = __fmaf_rn(-m2, p2.y, x0i);
+    const float c2r = __fmaf_rn(sm1, p1.x, b3r), c2i = __fmaf_rn(m1, p1.y, b3i);
+    const float d3r = __fmaf_rn(-sm1, p1.x, b3r), d3i = __fmaf_rn(-m1, p1.y, b3i);
+    a0 = make_float2(__fmaf_rn(c2r, 1.0f, c0r), __fmaf_rn(c2i, 1.0f, c0i));
+    a1 = make_float2(__fmaf_rn(c2r, -1.0f, c0r), __fmaf_rn(c2i, -1.0f, c0i));
+    a2 = make_float2(__fmaf_rn(d3i, sgn, c1r), __fmaf_rn(d3r, -sgn, c1i));
+    a3 = make_float2(__fmaf_rn(d3i, -sgn, c1r), __fmaf_rn(d3r, sgn, c1i));
+  }
+};
+
+template <int PREC, bool SCALED> struct Bfly4Packed {
+  using B = BflyPacked<PREC, SCALED>;
+  static constexpr uint32_t kOne = PREC == kFP16 ? 0x3C003C00u : 0x3F803F80u;
+  static constexpr uint32_t kQuarter = PREC == kFP16 ? 0x34003400u : 0x3E803E80u;
+  static __device__ __forceinline__ uint32_t pre(const uint32_t b, const uint4 e) {
+    const uint32_t X = __byte_perm(b, b, e.z);
+    const uint32_t Y = __byte_perm(X, X, 0x1032);
+    return B::fma2(e.x, X, Y);
+  }
+  // sgn: the half pair (lo s, hi -s) with s = -1 forward, +1 inverse
+  static __device__ __forceinline__ void run(uint32_t &a0, uint32_t &a1, uint32_t &a2, uint32_t &a3, const uint4 e1,
+                                             const uint4 e2, const uint4 e3, const uint32_t sgn) {
+    const uint32_t p1 = pre(a1, e1), p2 = pre(a2, e2), p3 = pre(a3, e3);
+    uint32_t x0 = a0;
+    if (SCALED) x0 = B::mul2(a0, kQuarter);
+    const uint32_t b3 = B::mul2(e3.y, p3);
+    const uint32_t c0 = B::fma2(e2.y, p2, x0), c1 = B::fma2(e2.w, p2, x0);
+    const uint32_t c2 = B::fma2(e1.y, p1, b3), d3 = B::fma2(e1.w, p1, b3);
+    const uint32_t D = __byte_perm(d3, d3, 0x1032);   // (d3i, d3r)
+    a0 = B::fma2(c2, kOne, c0);
+    a1 = B::fma2(c2, kOne ^ 0x80008000u, c0);
+    a2 = B::fma2(D, sgn, c1);
+    a3 = B::fma2(D, sgn ^ 0x80008000u, c1);
+  }
+};
+
+template <bool SCALED> struct Bfly4<kFP16, SCALED> : Bfly4Packed<kFP16, SCALED> {};
+template <bool SCALED> struct Bfly4<kBF16, SCALED> : Bfly4Packed<kBF16, SCALED> {};
+
 }  // namespace dsfft

@@ -35,9 +35,17 @@ __host__ __device__ constexpr uint32_t batch_path_code(int prec, int log2n, bool
 constexpr int kMaxLog2N = 24;
 constexpr int kFusedMaxLog2N = 14;   // whole transform staged on chip
 
-cudaError_t launch_build_table(int log2n, int fac, double eps, int prec, int inverse, int scaled,
+// Packed table entries for k in [0, count), multiplier times mscale (1, 1/2
+// or 1/4).
+cudaError_t launch_build_table(int log2n, int64_t count, int fac, double eps, int prec, int inverse, double mscale,
                                uint4 *out, int *counts, cudaStream_t stream);
 cudaError_t launch_per_pass_table(int log2n, const uint4 *table, uint4 *twp, cudaStream_t stream);
+
+// Radix-4 passes (at levels par, par + 2, ..., par = log2 N mod 2; one
+// radix-2 pass at level 0 first when log2 N is odd): offset of level l in
+// the per-pass radix-4 table, which holds N - 1 - par entries in all.
+__host__ __device__ constexpr int64_t r4_offset(int l, int par) { return (int64_t(1) << l) - 1 - par; }
+cudaError_t launch_per_pass_table4(int log2n, const uint4 *table4, uint4 *twp4, cudaStream_t stream);
 cudaError_t launch_fp64_table(int log2n, int fac, double eps, double *t, double *m, int *path,
                               cudaStream_t stream);
 
@@ -91,10 +99,19 @@ struct PlanView {
   int scale[2];
   const uint4 *twp[2];
   const Stage0Twiddles *tw0[2];   // host copies of the first per-pass entries
+  int radix;                      // 2 or 4
 };
 
 bool plan_view(const ::fft_plan *p, PlanView *v);
 void set_last_error(const char *msg);
+
+// Radix-4 fused kernel (N <= 2^14): per-pass radix-4 table and first-stage
+// twiddles (fused4.cuh); `inverse` selects the +i of the inverse butterflies.
+struct Stage0R4;
+FusedShape fused4_shape(int prec, int log2n);
+cudaError_t prepare_fused4(int prec, int log2n);
+cudaError_t launch_fused4(int prec, int log2n, bool scaled, int inverse, const void *in, void *out, int64_t batch,
+                          const uint4 *twp4, const Stage0R4 &tw0, cudaStream_t stream);
 
 // Persistent mixed-size batch kernel (N <= 2^14, any precision).
 int batch_tile_capacity(int prec, int log2n);

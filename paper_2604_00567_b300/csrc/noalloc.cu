@@ -96,6 +96,7 @@ extern "C" fft_status fft_exec_batch_noalloc(const fft_noalloc_item *items, int6
     if (!plan_view(it.plan, &v)) return FFT_ERR_INVALID_ARG;
     if (it.direction != FFT_FORWARD && it.direction != FFT_INVERSE) return FFT_ERR_INVALID_ARG;
     if (it.reserved != 0 || !it.in || !it.out) return FFT_ERR_INVALID_ARG;
+    if (v.radix != 2) return fail(FFT_ERR_UNSUPPORTED, "fft_exec_batch_noalloc: radix-4 plans are not batched");
     const uintptr_t eb = v.prec == kFP32 ? 8 : 4;
     if (((uintptr_t)it.in % eb) != 0 || ((uintptr_t)it.out % eb) != 0) return FFT_ERR_INVALID_ARG;
     if (v.kernel == 1 && it.in == it.out)

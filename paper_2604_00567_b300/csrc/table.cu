@@ -1,7 +1,8 @@
 // table.cu — FP64 twiddle-table builder (Algorithm 1 and the two single
 // factorizations of Eqs. 4-6 and 7-9), run on the GPU once per plan.
 //
-// For k in [0, N/2): theta = (-2 pi k)/N in FP64 (evaluated in that order,
+// For k in [0, count) (N/2 for the radix-2 table, 3N/4 for the radix-4
+// table, whose W^3j products pass -pi): theta = (-2 pi k)/N in FP64 (evaluated in that order,
 // so the entries of N are every (Nmax/N)-th entry of the table of Nmax),
 // w_r = cos theta, w_i = sin theta.  Selection:
 //   dual-select : cosine path when |w_r| >= |w_i| (Algorithm 1), else sine
@@ -9,8 +10,9 @@
 //   cosine      : cosine path
 // cosine path: m = w_r, t = w_i / w_r ; sine path: m = w_i, t = w_r / w_i.
 // The inverse direction conjugates W (w_i -> -w_i) after the clamp; a scaled
-// direction stores m/2.  t and m are then rounded ONCE (cvt.rn) from FP64
-// to the plan precision and packed (layout in common.cuh).
+// direction stores m/2 (radix-2 passes) or m/4 (radix-4 passes).  t and m
+// are then rounded ONCE (cvt.rn) from FP64 to the plan precision and packed
+// (layout in common.cuh).
 #include "common.cuh"
 #include "internal.h"
 
@@ -58,13 +60,12 @@ __device__ __forceinline__ Fp64Entry fp64_entry(int64_t k, int log2n, int fac, d
   return e;
 }
 
-__global__ void build_table_kernel(int log2n, int fac, double eps, int prec, int inverse, int scaled,
-                                   uint4 *__restrict__ out, int *__restrict__ counts) {
-  const int64_t half = 1LL << (log2n - 1);
+__global__ void build_table_kernel(int log2n, int64_t count, int fac, double eps, int prec, int inverse,
+                                   double mscale, uint4 *__restrict__ out, int *__restrict__ counts) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= half) return;
+  if (k >= count) return;
   Fp64Entry e = fp64_entry(k, log2n, fac, eps, inverse);
-  double m = scaled ? e.m * 0.5 : e.m;   // exact scaling by a power of two
+  double m = e.m * mscale;   // mscale is 1, 1/2 or 1/4: exact
   uint4 w;
   if (prec == kFP32) {
     const float tf = __double2float_rn(e.t);
@@ -115,12 +116,38 @@ __global__ void fp64_table_kernel(int log2n, int fac, double eps, double *t, dou
   path[k] = e.sine;
 }
 
-cudaError_t launch_build_table(int log2n, int fac, double eps, int prec, int inverse, int scaled,
+cudaError_t launch_build_table(int log2n, int64_t count, int fac, double eps, int prec, int inverse, double mscale,
                                uint4 *out, int *counts, cudaStream_t stream) {
-  const int64_t half = 1LL << (log2n - 1);
+  if (count <= 0) return cudaSuccess;
   const int threads = 256;
-  const unsigned blocks = (unsigned)((half + threads - 1) / threads);
-  build_table_kernel<<<blocks, threads, 0, stream>>>(log2n, fac, eps, prec, inverse, scaled, out, counts);
+  const unsigned blocks = (unsigned)((count + threads - 1) / threads);
+  build_table_kernel<<<blocks, threads, 0, stream>>>(log2n, count, fac, eps, prec, inverse, mscale, out, counts);
+  return cudaGetLastError();
+}
+
+// Per-pass copy for the radix-4 passes (levels l = par, par + 2, ..., log2 N
+// - 2 with par = log2 N mod 2, span L = 2^l): level l occupies
+// [r4_offset(l), r4_offset(l) + 3L) as three runs of L entries, run q - 1
+// holding W_4L^(q j) = table4[q j N/(4L)] for j in [0, L), q = 1, 2, 3.
+__global__ void per_pass_table4_kernel(int log2n, const uint4 *__restrict__ table4, uint4 *__restrict__ twp4) {
+  const int par = log2n & 1;
+  const int64_t total = (1LL << log2n) - 1 - par;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  int l = par;
+  while (r4_offset(l + 2, par) <= i) l += 2;
+  const int64_t L = 1LL << l;
+  const int64_t rem = i - r4_offset(l, par);
+  const int64_t q = rem / L + 1, j = rem % L;
+  twp4[i] = table4[(q * j) << (log2n - l - 2)];
+}
+
+cudaError_t launch_per_pass_table4(int log2n, const uint4 *table4, uint4 *twp4, cudaStream_t stream) {
+  const int64_t cnt = (1LL << log2n) - 1 - (log2n & 1);
+  if (cnt <= 0) return cudaSuccess;
+  const int threads = 256;
+  const unsigned blocks = (unsigned)((cnt + threads - 1) / threads);
+  per_pass_table4_kernel<<<blocks, threads, 0, stream>>>(log2n, table4, twp4);
   return cudaGetLastError();
 }
 

@@ -53,7 +53,7 @@ def test_opts_defaults(lib):
     o = dsfft.PlanOpts()
     assert lib.fft_plan_opts_init(1, ctypes.byref(o)) == 0
     assert o.lf_eps == 1e-7 and o.scale_forward == 1 and o.scale_inverse == 0 and o.device == -1
-    assert o.autotune == 0 and o.variant == 0
+    assert o.autotune == 0 and o.variant == 0 and o.radix == 0
     assert lib.fft_plan_opts_init(0, ctypes.byref(o)) == 0
     assert o.scale_forward == 0
     assert lib.fft_plan_opts_init(7, ctypes.byref(o)) == 1
@@ -75,8 +75,15 @@ def test_host_side_validation_without_gpu(lib):
     o.lf_eps = 0.0
     assert lib.fft_plan_create(ctypes.byref(h), 1024, 0, 0, ctypes.byref(o)) == 1
     lib.fft_plan_opts_init(0, ctypes.byref(o))
-    o.reserved[2] = 5
+    o.reserved[1] = 5
     assert lib.fft_plan_create(ctypes.byref(h), 1024, 0, 2, ctypes.byref(o)) == 1
+    lib.fft_plan_opts_init(0, ctypes.byref(o))
+    o.radix = 3
+    assert lib.fft_plan_create(ctypes.byref(h), 1024, 0, 2, ctypes.byref(o)) == 1
+    o.radix = 4
+    assert lib.fft_plan_create(ctypes.byref(h), 1 << 15, 0, 2, ctypes.byref(o)) == 3   # radix-4: N <= 2^14
+    o.variant = 2
+    assert lib.fft_plan_create(ctypes.byref(h), 1024, 0, 2, ctypes.byref(o)) == 3      # radix-4: fused wide only
     lib.fft_plan_opts_init(0, ctypes.byref(o))
     o.scale_forward = 3
     assert lib.fft_plan_create(ctypes.byref(h), 1024, 0, 2, ctypes.byref(o)) == 1
@@ -94,6 +101,7 @@ def test_host_side_validation_without_gpu(lib):
     assert lib.fft_plan_destroy(None) == 0
     assert lib.fft_plan_get_info(None, None) == 1
     assert lib.fft_plan_get_table(None, -1, None, 0) == 1
+    assert lib.fft_plan_get_table4(None, -1, None, 0) == 1
     assert lib.fft_status_string(2).decode().startswith("invalid size")
     assert lib.fft_status_string(99).decode() == "unknown status"
 
