@@ -13,6 +13,7 @@ Also reported on the same JSON line:
   per_n        : transforms/s, GB/s, fraction of roofline, and relative L2
                  error vs an FP64 FFT (numpy) on sampled signals, per N;
   fp32_plain   : the FP32 form (no scaling) on the same bytes per N;
+  radix4_fp16  : radix-4 dual-select plans (N <= 2^14) on the same FP16 batches;
   e2e          : the same metric with the input copied from pinned host
                  memory and the output copied back inside the timed region;
   cpu_baseline : the CPU oracle (op-by-op emulation) on a bounded sample;
@@ -289,6 +290,27 @@ def run_ours(args):
                           "rel_l2_vs_fp64": error_vs_fp64(p32, x32, y32, l, "fp32", False)}
         del x32, y32, p32
 
+    # radix-4 dual-select plans (N <= 2^14) on the same FP16 batches
+    radix4 = {}
+    for l in log2ns:
+        if l > 14:
+            continue
+        p4 = dsfft.Plan(1 << l, PRECISION, FACTORIZATION, radix=4)
+        for _ in range(3):
+            p4.exec(xs[l], out=ys[l])
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(max(3, K)):
+            p4.exec(xs[l], out=ys[l])
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / max(3, K)
+        nb = 2 * batch_for(l) * (4 << l)
+        radix4[f"2^{l}"] = {"transforms_per_s": batch_for(l) / (ms / 1e3), "GB_per_s": round(nb / (ms / 1e3) / 1e9, 1),
+                            "frac_of_hbm": round(nb / (ms / 1e3) / 1e9 / hbm_peak, 4),
+                            "rel_l2_vs_fp64": error_vs_fp64(p4, xs[l], ys[l], l, PRECISION, True)}
+        del p4
+
     # end to end: pinned host input -> device -> FFT -> host, every step
     e2e_steps = max(1, min(K, 3))
     host_in = {l: xs[l].cpu().pin_memory() for l in log2ns}
@@ -328,7 +350,7 @@ def run_ours(args):
                        "precision": PRECISION, "factorization": FACTORIZATION,
                        "input": "re/im i.i.d. uniform[-1,1], torch.Generator seeded",
                        "l2": "inputs 1 GiB per launch > 126 MB L2; no flush", "parallelism": f"replicas{world}"},
-            "roofline": roofline, "per_n": per_n, "fp32_plain": fp32, "e2e": e2e,
+            "roofline": roofline, "per_n": per_n, "fp32_plain": fp32, "radix4_fp16": radix4, "e2e": e2e,
             "gpu_launches": K * sum(plans[l].info()["launches"] for l in log2ns),
             "clocks": clocks, "cpu_baseline": cpu, "serve": serve,
         }

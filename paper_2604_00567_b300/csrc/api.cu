@@ -90,8 +90,7 @@ int default_variant(int prec, int log2n) {
                                       : ((log2n >= 5 && log2n <= 8) || log2n == 11 || log2n == 12);
     return narrow && fused_has_narrow(prec, log2n) ? FFT_VARIANT_FUSED_NARROW : FFT_VARIANT_FUSED_WIDE;
   }
-  if (log2n == 16) return FFT_VARIANT_SWEEPS;
-  return cluster_log2k(prec, log2n) >= 0 ? FFT_VARIANT_CLUSTER : FFT_VARIANT_SWEEPS;
+  return log2n == 15 ? FFT_VARIANT_CLUSTER : FFT_VARIANT_SWEEPS;
 }
 
 // Make the plan run variant v (valid for its size): kernel choice and the
@@ -398,47 +397,53 @@ fft_status fft_plan_create(fft_plan **plan, int64_t n, fft_precision prec, fft_f
   p->radix = radix;
 
   const size_t entries = (size_t)(n / 2);
+  // per-pass tables hold the compact 8-byte entries for FP16/BF16
+  const int compact = prec == kFP32 ? 0 : 1;
+  const size_t tw_bytes = compact ? sizeof(uint2) : sizeof(uint4);
   int *counts = nullptr;
+  uint4 *head = nullptr;      // 16-byte forms of the first-stage entries: [dir][radix 2/4][31]
   cudaStream_t st = nullptr;
   fft_status status = FFT_OK;
   int host_counts[2] = {0, 0};
   do {
     if ((e = cudaMalloc(&p->table[0], entries * sizeof(uint4))) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc table"); break; }
     if ((e = cudaMalloc(&p->table[1], entries * sizeof(uint4))) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc table"); break; }
-    if ((e = cudaMalloc(&p->twp[0], (size_t)(n - 1) * sizeof(uint4))) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc table"); break; }
-    if ((e = cudaMalloc(&p->twp[1], (size_t)(n - 1) * sizeof(uint4))) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc table"); break; }
+    if ((e = cudaMalloc(&p->twp[0], (size_t)(n - 1) * tw_bytes)) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc table"); break; }
+    if ((e = cudaMalloc(&p->twp[1], (size_t)(n - 1) * tw_bytes)) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc table"); break; }
     if ((e = cudaMalloc(&counts, 2 * sizeof(int))) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc counts"); break; }
+    if ((e = cudaMalloc(&head, 4 * 31 * sizeof(uint4))) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc"); break; }
     if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) { status = cuda_fail(e, "stream"); break; }
     if ((e = cudaMemsetAsync(counts, 0, 2 * sizeof(int), st)) != cudaSuccess) { status = cuda_fail(e, "memset"); break; }
     if ((e = launch_build_table(log2n, n / 2, fac, opts.lf_eps, prec, 0, p->scale[0] ? 0.5 : 1.0, p->table[0], counts, st)) != cudaSuccess) { status = cuda_fail(e, "table build"); break; }
     if ((e = launch_build_table(log2n, n / 2, fac, opts.lf_eps, prec, 1, p->scale[1] ? 0.5 : 1.0, p->table[1], nullptr, st)) != cudaSuccess) { status = cuda_fail(e, "table build"); break; }
-    if ((e = launch_per_pass_table(log2n, p->table[0], p->twp[0], st)) != cudaSuccess) { status = cuda_fail(e, "per-pass table"); break; }
-    if ((e = launch_per_pass_table(log2n, p->table[1], p->twp[1], st)) != cudaSuccess) { status = cuda_fail(e, "per-pass table"); break; }
-    for (int d = 0; d < 2; ++d) {
-      const size_t cnt = (size_t)((n < 32 ? n : 32) - 1);
-      if ((e = cudaMemcpyAsync(p->tw0[d].e, p->twp[d], cnt * sizeof(uint4), cudaMemcpyDeviceToHost, st)) != cudaSuccess) break;
+    const int64_t cnt0 = (n < 32 ? n : 32) - 1;
+    for (int d = 0; d < 2 && e == cudaSuccess; ++d) {
+      if ((e = launch_per_pass_table(log2n, p->table[d], p->twp[d], n - 1, compact, st)) != cudaSuccess) break;
+      if ((e = launch_per_pass_table(log2n, p->table[d], head + d * 62, cnt0, 0, st)) != cudaSuccess) break;
+      e = cudaMemcpyAsync(p->tw0[d].e, head + d * 62, (size_t)cnt0 * sizeof(uint4), cudaMemcpyDeviceToHost, st);
     }
-    if (e != cudaSuccess) { status = cuda_fail(e, "copy stage-0 twiddles"); break; }
+    if (e != cudaSuccess) { status = cuda_fail(e, "per-pass table"); break; }
     if ((e = cudaMemcpyAsync(host_counts, counts, 2 * sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess) { status = cuda_fail(e, "copy counts"); break; }
     if (radix == 4) {
       const int64_t c4 = 3 * n / 4, p4 = n - 1 - (log2n & 1);
       for (int d = 0; d < 2 && e == cudaSuccess; ++d) {
         if ((e = cudaMalloc(&p->table4[d], (size_t)(c4 > 0 ? c4 : 1) * sizeof(uint4))) != cudaSuccess) break;
-        if ((e = cudaMalloc(&p->twp4[d], (size_t)(p4 > 0 ? p4 : 1) * sizeof(uint4))) != cudaSuccess) break;
+        if ((e = cudaMalloc(&p->twp4[d], (size_t)(p4 > 0 ? p4 : 1) * tw_bytes)) != cudaSuccess) break;
         if ((e = launch_build_table(log2n, c4, fac, opts.lf_eps, prec, d, p->scale[d] ? 0.25 : 1.0, p->table4[d],
                                     nullptr, st)) != cudaSuccess)
           break;
-        if ((e = launch_per_pass_table4(log2n, p->table4[d], p->twp4[d], st)) != cudaSuccess) break;
-        memset(&p->s0r4[d], 0, sizeof(Stage0R4));
-        p->s0r4[d].r2 = p->tw0[d].e[0];
+        if ((e = launch_per_pass_table4(log2n, p->table4[d], p->twp4[d], p4, compact, st)) != cudaSuccess) break;
         const int64_t cnt = p4 < 31 ? p4 : 31;
-        if (cnt > 0 && (e = cudaMemcpyAsync(p->s0r4[d].e, p->twp4[d], (size_t)cnt * sizeof(uint4),
+        if ((e = launch_per_pass_table4(log2n, p->table4[d], head + d * 62 + 31, cnt, 0, st)) != cudaSuccess) break;
+        memset(&p->s0r4[d], 0, sizeof(Stage0R4));
+        if (cnt > 0 && (e = cudaMemcpyAsync(p->s0r4[d].e, head + d * 62 + 31, (size_t)cnt * sizeof(uint4),
                                             cudaMemcpyDeviceToHost, st)) != cudaSuccess)
           break;
       }
       if (e != cudaSuccess) { status = cuda_fail(e, "radix-4 tables"); break; }
     }
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) { status = cuda_fail(e, "table build sync"); break; }
+    for (int d = 0; d < 2; ++d) p->s0r4[d].r2 = p->tw0[d].e[0];
     if (radix == 4) {
       p->variant = FFT_VARIANT_FUSED_WIDE;
       p->kernel = 0;
@@ -452,6 +457,7 @@ fft_status fft_plan_create(fft_plan **plan, int64_t n, fft_precision prec, fft_f
   } while (0);
   if (st) cudaStreamDestroy(st);
   if (counts) cudaFree(counts);
+  if (head) cudaFree(head);
   if (status != FFT_OK) {
     for (int d = 0; d < 2; ++d) {
       if (p->table[d]) cudaFree(p->table[d]);
@@ -542,8 +548,9 @@ fft_status fft_plan_get_info(const fft_plan *plan, fft_plan_info *info) {
   info->points_per_thread = 1 << plan->shape.log2r;
   info->threads_per_transform = plan->shape.threads_per_transform;
   info->transforms_per_block = plan->shape.transforms_per_block;
-  info->table_bytes = (int64_t)2 * (plan->n / 2 + plan->n - 1) * (int64_t)sizeof(uint4);
-  if (plan->radix == 4) info->table_bytes += (int64_t)2 * (3 * plan->n / 4 + plan->n - 1) * (int64_t)sizeof(uint4);
+  const int64_t twb = plan->prec == kFP32 ? (int64_t)sizeof(uint4) : (int64_t)sizeof(uint2);
+  info->table_bytes = (int64_t)2 * (plan->n / 2 * (int64_t)sizeof(uint4) + (plan->n - 1) * twb);
+  if (plan->radix == 4) info->table_bytes += (int64_t)2 * (3 * plan->n / 4 * (int64_t)sizeof(uint4) + plan->n * twb);
   info->element_bytes = (int64_t)elem_bytes(plan->prec);
   info->scale_forward = plan->scale[0];
   info->scale_inverse = plan->scale[1];

@@ -25,7 +25,7 @@ __device__ __forceinline__ void batch_tile(const BatchTile &t, const BatchItem *
   static_assert(K::NSTAGES == 1 || K::TPC * K::PADN * (int)sizeof(typename K::E) <= kBatchSmem, "tile fits");
   using E = typename K::E;
   const uint4 *tw = t.twp;
-  K::run_tile(GatherIO<E>{items + t.first}, (int)t.count, tw, [tw](int i) { return __ldg(tw + i); },
+  K::run_tile(GatherIO<E>{items + t.first}, (int)t.count, tw, [tw](int i) { return tw_load<PREC>(tw, i); },
               reinterpret_cast<E *>(smem));
 }
 

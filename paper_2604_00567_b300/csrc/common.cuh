@@ -76,6 +76,33 @@ struct GatherIO {
   __device__ __forceinline__ E *dst(int64_t k) const { return static_cast<E *>(items[k].out); }
 };
 
+// Per-pass twiddle entries as the kernels read them.  FP32: the 16-byte
+// packed entry above.  FP16/BF16: a compact 8-byte entry
+//   x = selector (low half) | t (high half),  y = (lo sigma*m, hi m)
+// from which tw_unpack rebuilds the 16-byte form with three integer
+// operations ((-t, t) by a sign flip and a byte permute, -(sigma m, m) by a
+// sign flip); the permute that uses the selector reads only its low 16 bits.
+// Half the bytes per entry halves the L1/L2 traffic of the later register
+// stages, whose lanes each read a different entry.
+template <int PREC> struct TwEntry { using T = uint4; };
+template <> struct TwEntry<kFP16> { using T = uint2; };
+template <> struct TwEntry<kBF16> { using T = uint2; };
+
+__device__ __forceinline__ uint4 tw_unpack(const uint4 e) { return e; }
+__device__ __forceinline__ uint4 tw_unpack(const uint2 e) {
+  uint4 r;
+  r.x = __byte_perm(e.x, e.x ^ 0x80000000u, 0x3276);   // (lo -t, hi t)
+  r.y = e.y;
+  r.z = e.x;
+  r.w = e.y ^ 0x80008000u;
+  return r;
+}
+// Entry i of a per-pass table (the table's storage is TwEntry<PREC>::T[]).
+template <int PREC>
+__device__ __forceinline__ uint4 tw_load(const uint4 *table, int64_t i) {
+  return tw_unpack(__ldg(reinterpret_cast<const typename TwEntry<PREC>::T *>(table) + i));
+}
+
 // Storage type of one complex element.
 template <int PREC> struct Elem;
 template <> struct Elem<kFP32> { using T = float2; };

@@ -19,8 +19,9 @@
 //
 // Twiddles come from the plan's per-pass table: pass p uses entries
 // twp[2^p - 1 + j] = table[j N/2^(p+1)], j in [0, 2^p) (exact copies of the
-// rounded entries), so the lanes of a warp, which hold consecutive j, read
-// consecutive 16-byte entries.
+// rounded entries; 8-byte compact entries for FP16/BF16, see common.cuh),
+// so the lanes of a warp, which hold consecutive j, read consecutive
+// entries.
 #pragma once
 
 #include "common.cuh"
@@ -95,7 +96,7 @@ struct Fused {
           // constant bank
           uint4 e;
           if constexpr (P == 0) e = tw0(((1 << i) - 1) + ql);
-          else e = __ldg(tw + ((1 << (P + i)) - 1) + j + (ql << P));
+          else e = tw_load<PREC>(tw, ((1 << (P + i)) - 1) + j + (ql << P));
           constexpr int qtop = bitrev(ql, i) << (RHO - i);
           static_for<0, half>([&](auto qh_) {
             constexpr int q = qtop | decltype(qh_)::value;

@@ -80,7 +80,7 @@ struct Fused4 : Fused<PREC, LOG2N, LOG2R, SCALED, BT> {
         constexpr int lvl = P + i;
         constexpr int L = 1 << lvl;
         constexpr int Q = 1 << (RHO - i - 2);
-        const uint4 *base = tw + r4_offset(lvl, PAR) + j;
+        const int base = (int)r4_offset(lvl, PAR) + j;
         static_for<0, (1 << i)>([&](auto ql_) {
           constexpr int ql = decltype(ql_)::value;
           uint4 e1, e2, e3;
@@ -90,9 +90,9 @@ struct Fused4 : Fused<PREC, LOG2N, LOG2R, SCALED, BT> {
             e2 = tw0.e[o + L];
             e3 = tw0.e[o + 2 * L];
           } else {
-            e1 = __ldg(base + (ql << P));
-            e2 = __ldg(base + (ql << P) + L);
-            e3 = __ldg(base + (ql << P) + 2 * L);
+            e1 = tw_load<PREC>(tw, base + (ql << P));
+            e2 = tw_load<PREC>(tw, base + (ql << P) + L);
+            e3 = tw_load<PREC>(tw, base + (ql << P) + 2 * L);
           }
           constexpr int qtop = bitrev(ql, i) << (RHO - i);
           static_for<0, Q>([&](auto qh_) {

@@ -42,12 +42,12 @@ struct GroupPasses {
         constexpr int i = decltype(i_)::value;
         constexpr int half = 1 << (RHO - 1 - i);
         constexpr int p = P0 + PL + i;                     // global pass
-        const uint4 *tp = twp + ((1 << p) - 1) + jg + (jloc << P0);
+        const int tp = ((1 << p) - 1) + jg + (jloc << P0);
         static_for<0, (1 << i)>([&](auto ql_) {
           constexpr int ql = decltype(ql_)::value;
           uint4 e;
           if constexpr (P0 == 0 && PL == 0) e = tw0(((1 << i) - 1) + ql);
-          else e = __ldg(tp + (ql << (PL + P0)));
+          else e = tw_load<PREC>(twp, tp + (ql << (PL + P0)));
           constexpr int qtop = bitrev(ql, i) << (RHO - i);
           static_for<0, half>([&](auto qh_) {
             constexpr int q = qtop | decltype(qh_)::value;

@@ -63,10 +63,10 @@ struct Sweep {
         constexpr int i = decltype(i_)::value;
         constexpr int half = 1 << (RHO - 1 - i);
         const int p = x.P0 + PL + i;                       // global pass
-        const uint4 *tp = twp + ((1LL << p) - 1) + x.jg + (jloc << x.P0);
+        const int64_t tp = ((1LL << p) - 1) + x.jg + (jloc << x.P0);
         static_for<0, (1 << i)>([&](auto ql_) {
           constexpr int ql = decltype(ql_)::value;
-          const uint4 e = __ldg(tp + ((int64_t)ql << (PL + x.P0)));
+          const uint4 e = tw_load<PREC>(twp, tp + ((int64_t)ql << (PL + x.P0)));
           constexpr int qtop = bitrev(ql, i) << (RHO - i);
           static_for<0, half>([&](auto qh_) {
             constexpr int q = qtop | decltype(qh_)::value;
