@@ -111,8 +111,9 @@ typedef struct fft_plan_opts {
     int32_t variant;        /* fft_variant; a variant the size does not have
                                gives FFT_ERR_UNSUPPORTED */
     /* 0 or 2: radix-2 passes (the paper's algorithm).  4: radix-4 passes
-     * (the radix-4 extension the paper's Discussion proposes; N <= 2^14,
-     * fused kernel only, otherwise FFT_ERR_UNSUPPORTED): each radix-4 pass
+     * (the radix-4 extension the paper's Discussion proposes; the fused
+     * kernel for N <= 2^14, two HBM sweeps of radix-4 passes above; other
+     * variants give FFT_ERR_UNSUPPORTED): each radix-4 pass
      * (span L) maps Z[q N/4 + s L + j], q = 0..3, to
      * Y[4 s L + p L + j] = sum_q W_4L^(q j) Z[...] (-i)^(q p) (+i inverse);
      * each of its three twiddle products uses the 6-FMA form of its own

@@ -109,8 +109,11 @@ cudaError_t apply_variant(fft_plan *p, int v) {
 // Queue one transform batch of plan p on `stream` (d: 0 forward, 1 inverse).
 cudaError_t plan_launch(const fft_plan *p, const void *in, void *out, int64_t batch, int d, cudaStream_t stream) {
   const bool scaled = p->scale[d] != 0;
-  if (p->radix == 4)
+  if (p->radix == 4) {
+    if (p->kernel == 1)
+      return launch_sweeps4(p->prec, p->log2n, scaled, d, in, out, nullptr, batch, p->twp4[d], p->s0r4[d].r2, stream);
     return launch_fused4(p->prec, p->log2n, scaled, d, in, out, batch, p->twp4[d], p->s0r4[d], stream);
+  }
   if (p->kernel == 0)
     return launch_fused(p->prec, p->log2n, p->narrow, scaled, in, out, batch, p->twp[d], p->tw0[d], stream);
   if (p->kernel == 2)
@@ -367,12 +370,10 @@ fft_status fft_plan_create(fft_plan **plan, int64_t n, fft_precision prec, fft_f
   const int log2n = ilog2_exact(n);
   if (log2n < 1 || log2n > kMaxLog2N) return FFT_ERR_INVALID_SIZE;
   const int radix = opts.radix == 4 ? 4 : 2;
-  if (radix == 4 && log2n > kFusedMaxLog2N) {
-    snprintf(g_last_error, sizeof g_last_error, "radix-4 passes are implemented for N <= 2^%d", kFusedMaxLog2N);
-    return FFT_ERR_UNSUPPORTED;
-  }
-  if (radix == 4 && opts.variant != FFT_VARIANT_AUTO && opts.variant != FFT_VARIANT_FUSED_WIDE) {
-    snprintf(g_last_error, sizeof g_last_error, "radix-4 plans run the fused radix-4 kernel only");
+  const int r4_variant = log2n <= kFusedMaxLog2N ? FFT_VARIANT_FUSED_WIDE : FFT_VARIANT_SWEEPS;
+  if (radix == 4 && opts.variant != FFT_VARIANT_AUTO && opts.variant != r4_variant) {
+    snprintf(g_last_error, sizeof g_last_error, "radix-4 plans run the fused radix-4 kernel (N <= 2^%d) or "
+             "radix-4 sweeps", kFusedMaxLog2N);
     return FFT_ERR_UNSUPPORTED;
   }
   if (opts.variant != FFT_VARIANT_AUTO && !variant_valid(prec, log2n, opts.variant)) {
@@ -446,10 +447,17 @@ fft_status fft_plan_create(fft_plan **plan, int64_t n, fft_precision prec, fft_f
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) { status = cuda_fail(e, "table build sync"); break; }
     for (int d = 0; d < 2; ++d) p->s0r4[d].r2 = p->tw0[d].e[0];
     if (radix == 4) {
-      p->variant = FFT_VARIANT_FUSED_WIDE;
-      p->kernel = 0;
-      p->shape = fused4_shape(prec, log2n);
-      if ((e = prepare_fused4(prec, log2n)) != cudaSuccess) { status = cuda_fail(e, "kernel attributes"); break; }
+      p->variant = r4_variant;
+      if (log2n <= kFusedMaxLog2N) {
+        p->kernel = 0;
+        p->shape = fused4_shape(prec, log2n);
+        e = prepare_fused4(prec, log2n);
+      } else {
+        p->kernel = 1;
+        p->shape = fused_shape(prec, kFusedMaxLog2N, false);
+        e = prepare_sweeps4(prec, log2n);
+      }
+      if (e != cudaSuccess) { status = cuda_fail(e, "kernel attributes"); break; }
       break;
     }
     const int v = opts.variant != FFT_VARIANT_AUTO ? opts.variant : default_variant(prec, log2n);

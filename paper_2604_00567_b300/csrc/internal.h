@@ -87,6 +87,15 @@ cudaError_t prepare_sweeps(int prec, int log2n);
 cudaError_t launch_sweeps(int prec, int log2n, bool scaled, const void *in, void *out, const BatchItem *items,
                           int64_t batch, const uint4 *twp, cudaStream_t stream);
 
+// Radix-4 plans, N > 2^14: two sweeps of whole radix-4 passes (sweep 1 also
+// holds the radix-2 pass of an odd log2 N); `twp4` the per-pass radix-4
+// table, `r2e` the radix-2 entry k = 0.
+void sweep_split4(int log2n, int *ls1, int *ls2);
+cudaError_t prepare_sweeps4(int prec, int log2n);
+cudaError_t launch_sweeps4(int prec, int log2n, bool scaled, int inverse, const void *in, void *out,
+                           const BatchItem *items, int64_t batch, const uint4 *twp4, const uint4 &r2e,
+                           cudaStream_t stream);
+
 // 2^15 <= N <= 2^17 (FP16/BF16) or <= 2^16 (FP32): one launch on a cluster
 // of 2^cluster_log2k CTAs whose distributed shared memory holds the
 // transform between the two halves of the passes.  -1 = not handled.

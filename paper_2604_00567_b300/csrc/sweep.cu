@@ -17,7 +17,7 @@
 // stages through shared memory laid out [element][group] (conflict-free).
 // Sweep 1's output of a block is one contiguous range of G 2^LS elements; it
 // is transposed through shared memory so that it is stored in order.
-#include "common.cuh"
+#include "fused4.cuh"
 #include "internal.h"
 
 namespace dsfft {
@@ -27,30 +27,85 @@ __device__ __forceinline__ uint32_t sw_ldcs(const uint32_t *p) { return __ldcs(r
 __device__ __forceinline__ void sw_stcs(float2 *p, float2 v) { __stcs(p, v); }
 __device__ __forceinline__ void sw_stcs(uint32_t *p, uint32_t v) { __stcs(reinterpret_cast<unsigned int *>(p), v); }
 
-template <int PREC, int LS, bool SCALED, bool LAST>
+// R4: radix-4 passes (the radix-4 extension, fused4.cuh): stages of whole
+// radix-4 passes with 16 points per thread; an odd LS (sweep 1 of an odd
+// log2 N) starts with the radix-2 pass of span 1.
+template <int PREC, int LS, bool SCALED, bool LAST, bool R4 = false>
 struct Sweep {
   using E = typename Elem<PREC>::T;
   static constexpr int EB = (int)sizeof(E);
-  static constexpr int LOG2R = PREC == kFP32 ? 4 : 5;
+  static constexpr int LOG2R = (R4 || PREC == kFP32) ? 4 : 5;
   static constexpr int R = 1 << LOG2R;
   static constexpr int M = 1 << LS;                      // elements per group
   static constexpr int T = M / R;                        // threads per group
-  // groups per block: at most 32, and a block's groups fill <= 128 KB
-  static constexpr int LOG2G_CAP = (PREC == kFP32 ? 14 : 15) - LS;
+  // groups per block: at most 32, and at most 1024 threads (R points each)
+  static constexpr int LOG2G_CAP = (LOG2R == 4 ? 14 : 15) - LS;
   static constexpr int LOG2G = LOG2G_CAP < 5 ? LOG2G_CAP : 5;
   static constexpr int G = 1 << LOG2G;
   static constexpr int TPB = G * T;
+  static_assert(TPB <= 1024, "one block holds at most 1024 threads");
   static constexpr int SMEM_X = G * M * EB;              // exchange buffer
   static constexpr int SMEM_T = LAST ? 0 : M * (G + 1) * EB;  // padded transpose buffer
   static constexpr int SMEM = SMEM_X > SMEM_T ? SMEM_X : SMEM_T;
-  static constexpr int NSTAGES = (LS + LOG2R - 1) / LOG2R;
+  using S4 = typename std::conditional<PREC == kFP32, float, uint32_t>::type;
 
   struct Ctx {
     int tid, lg;
     int64_t g;        // group index within the transform
     int64_t jg;       // g mod 2^P0
     int P0;
+    uint4 r2e;        // radix-4 plans: radix-2 entry k = 0 (W^0)
+    S4 sgn;           // radix-4 plans: sign operand of the +-i d3 terms
   };
+
+  // levels of the register stage starting at local level PL
+  static __host__ __device__ constexpr int stage_levels(int pl) {
+    return R4 ? r4_stage_levels(LS, LOG2R, pl) : ((LS - pl) < LOG2R ? (LS - pl) : LOG2R);
+  }
+
+  // radix-4 passes of one stage: local levels [PL, PL + RHO), global
+  // P0 + PL + ...; per-pass radix-4 entries r4_offset(lvl) + (q - 1) L + j
+  template <int PL, int RHO>
+  static __device__ __forceinline__ void compute4(E (&v)[R], const Ctx &x, const uint4 *__restrict__ twp) {
+    constexpr int C = R >> RHO;
+    constexpr bool R2 = PL == 0 && (LS & 1);
+    constexpr int I0 = R2 ? 1 : 0;
+    static_assert((RHO - I0) % 2 == 0, "a stage holds whole radix-4 passes");
+    const int par = (x.P0 + LS) & 1;    // log2 N mod 2 (sweep 2 starts at an even or odd level)
+    static_for<0, C>([&](auto c_) {
+      constexpr int c = decltype(c_)::value;
+      if constexpr (c > 0) asm volatile("" ::: "memory");
+      const int gl = x.tid + c * T;
+      const int64_t jloc = gl & ((1 << PL) - 1);
+      if constexpr (R2) {
+        constexpr int half = 1 << (RHO - 1);
+        static_for<0, half>([&](auto qh_) {
+          constexpr int q = decltype(qh_)::value;
+          Bfly<PREC, SCALED>::run(v[c + q * C], v[c + (q + half) * C], x.r2e);
+        });
+      }
+      static_for<0, (RHO - I0) / 2>([&](auto k_) {
+        constexpr int i = I0 + 2 * decltype(k_)::value;
+        constexpr int Q = 1 << (RHO - i - 2);
+        const int lvl = x.P0 + PL + i;
+        const int64_t L = 1LL << lvl;
+        const int64_t tp = ((1LL << lvl) - 1 - par) + x.jg + (jloc << x.P0);
+        static_for<0, (1 << i)>([&](auto ql_) {
+          constexpr int ql = decltype(ql_)::value;
+          const int64_t at = tp + ((int64_t)ql << (PL + x.P0));
+          const uint4 e1 = tw_load<PREC>(twp, at);
+          const uint4 e2 = tw_load<PREC>(twp, at + L);
+          const uint4 e3 = tw_load<PREC>(twp, at + 2 * L);
+          constexpr int qtop = bitrev(ql, i) << (RHO - i);
+          static_for<0, Q>([&](auto qh_) {
+            constexpr int q0 = qtop | decltype(qh_)::value;
+            Bfly4<PREC, SCALED>::run(v[c + q0 * C], v[c + (q0 + Q) * C], v[c + (q0 + 2 * Q) * C],
+                                     v[c + (q0 + 3 * Q) * C], e1, e2, e3, x.sgn);
+          });
+        });
+      });
+    });
+  }
 
   template <int PL, int RHO>
   static __device__ __forceinline__ void compute(E (&v)[R], const Ctx &x, const uint4 *__restrict__ twp) {
@@ -77,19 +132,19 @@ struct Sweep {
     });
   }
 
-  template <int S>
+  template <int PL>
   static __device__ __forceinline__ void stages(E (&v)[R], E *sm, const Ctx &x, const uint4 *__restrict__ twp,
                                                 E *dst, int64_t stride, bool active) {
-    constexpr int PL = S * LOG2R;
-    constexpr int RHO = (LS - PL) < LOG2R ? (LS - PL) : LOG2R;
+    constexpr int RHO = stage_levels(PL);
     constexpr int C = R >> RHO;
-    if constexpr (S > 0) {
+    if constexpr (PL > 0) {
       static_for<0, R>([&](auto p_) {
         constexpr int p = decltype(p_)::value;
         v[p] = sm[(x.tid + p * T) * G + x.lg];
       });
     }
-    compute<PL, RHO>(v, x, twp);
+    if constexpr (R4) compute4<PL, RHO>(v, x, twp);
+    else compute<PL, RHO>(v, x, twp);
     if constexpr (PL + RHO == LS) {
       // local output o = tid + c T + bitrev(q) C T
       if constexpr (LAST) {
@@ -104,7 +159,7 @@ struct Sweep {
           });
         }
       } else {
-        if constexpr (S > 0) __syncthreads();
+        if constexpr (PL > 0) __syncthreads();
         static_for<0, C>([&](auto c_) {
           constexpr int c = decltype(c_)::value;
           static_for<0, (1 << RHO)>([&](auto q_) {
@@ -126,7 +181,7 @@ struct Sweep {
         }
       }
     } else {
-      if constexpr (S > 0) __syncthreads();
+      if constexpr (PL > 0) __syncthreads();
       static_for<0, C>([&](auto c_) {
         constexpr int c = decltype(c_)::value;
         const int gl = x.tid + c * T;
@@ -137,17 +192,18 @@ struct Sweep {
         });
       });
       __syncthreads();
-      stages<S + 1>(v, sm, x, twp, dst, stride, active);
+      stages<PL + RHO>(v, sm, x, twp, dst, stride, active);
     }
   }
 };
 
 // Sweep 1 reads io.src and writes io.dst; sweep 2 (LAST) reads and writes
 // io.dst in place.
-template <int PREC, int LS, bool SCALED, bool LAST, class IO>
-__global__ void __launch_bounds__(Sweep<PREC, LS, SCALED, LAST>::TPB)
-    sweep_fft_kernel(const IO io, int64_t batch, int log2n, int P0, const uint4 *__restrict__ twp) {
-  using K = Sweep<PREC, LS, SCALED, LAST>;
+template <int PREC, int LS, bool SCALED, bool LAST, class IO, bool R4 = false>
+__global__ void __launch_bounds__(Sweep<PREC, LS, SCALED, LAST, R4>::TPB)
+    sweep_fft_kernel(const IO io, int64_t batch, int log2n, int P0, const uint4 *__restrict__ twp,
+                     const uint4 r2e, const uint32_t sgn_bits) {
+  using K = Sweep<PREC, LS, SCALED, LAST, R4>;
   using E = typename K::E;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   E *sm = reinterpret_cast<E *>(smem_raw);
@@ -162,6 +218,9 @@ __global__ void __launch_bounds__(Sweep<PREC, LS, SCALED, LAST>::TPB)
   x.g = g0 + x.lg;
   x.P0 = P0;
   x.jg = x.g & ((1LL << P0) - 1);
+  x.r2e = r2e;
+  if constexpr (PREC == kFP32) x.sgn = __uint_as_float(sgn_bits);
+  else x.sgn = sgn_bits;
   const bool active = tr < batch;
   E v[K::R];
   if (active) {
@@ -182,21 +241,22 @@ __global__ void __launch_bounds__(Sweep<PREC, LS, SCALED, LAST>::TPB)
 // ---------------------------------------------------------------------------
 // dispatch: LS in [7, 12] (N = 2^15 .. 2^24 split as ceil(m/2) + floor(m/2))
 
-template <int PREC, int LS, bool SCALED, bool LAST>
+template <int PREC, int LS, bool SCALED, bool LAST, bool R4>
 static cudaError_t launch_sweep_one(const void *in, void *out, const BatchItem *items, int64_t batch, int log2n,
-                                    int P0, const uint4 *twp, cudaStream_t stream) {
-  using K = Sweep<PREC, LS, SCALED, LAST>;
+                                    int P0, const uint4 *twp, const uint4 &r2e, uint32_t sgn, cudaStream_t stream) {
+  using K = Sweep<PREC, LS, SCALED, LAST, R4>;
   using E = typename K::E;
   const int64_t S = 1LL << (log2n - LS);
   if (S < K::G) return cudaErrorInvalidValue;
   const int64_t blocks = batch * (S >> K::LOG2G);
   if (blocks > 0x7FFFFFFF) return cudaErrorInvalidConfiguration;
   if (items) {
-    sweep_fft_kernel<PREC, LS, SCALED, LAST, GatherIO<E>><<<(unsigned)blocks, K::TPB, K::SMEM, stream>>>(
-        GatherIO<E>{items}, batch, log2n, P0, twp);
+    sweep_fft_kernel<PREC, LS, SCALED, LAST, GatherIO<E>, R4><<<(unsigned)blocks, K::TPB, K::SMEM, stream>>>(
+        GatherIO<E>{items}, batch, log2n, P0, twp, r2e, sgn);
   } else {
-    sweep_fft_kernel<PREC, LS, SCALED, LAST, ContigIO<E>><<<(unsigned)blocks, K::TPB, K::SMEM, stream>>>(
-        ContigIO<E>{static_cast<const E *>(in), static_cast<E *>(out), 1LL << log2n}, batch, log2n, P0, twp);
+    sweep_fft_kernel<PREC, LS, SCALED, LAST, ContigIO<E>, R4><<<(unsigned)blocks, K::TPB, K::SMEM, stream>>>(
+        ContigIO<E>{static_cast<const E *>(in), static_cast<E *>(out), 1LL << log2n}, batch, log2n, P0, twp, r2e,
+        sgn);
   }
   return cudaGetLastError();
 }
@@ -208,32 +268,32 @@ static cudaError_t prepare_sweep_kernel(F kern, int smem) {
   return cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
 }
 
-template <int PREC, int LS, bool SCALED, bool LAST>
+template <int PREC, int LS, bool SCALED, bool LAST, bool R4>
 static cudaError_t prepare_sweep_one() {
-  using K = Sweep<PREC, LS, SCALED, LAST>;
+  using K = Sweep<PREC, LS, SCALED, LAST, R4>;
   using E = typename K::E;
-  cudaError_t e = prepare_sweep_kernel(sweep_fft_kernel<PREC, LS, SCALED, LAST, ContigIO<E>>, K::SMEM);
+  cudaError_t e = prepare_sweep_kernel(sweep_fft_kernel<PREC, LS, SCALED, LAST, ContigIO<E>, R4>, K::SMEM);
   if (e != cudaSuccess) return e;
-  return prepare_sweep_kernel(sweep_fft_kernel<PREC, LS, SCALED, LAST, GatherIO<E>>, K::SMEM);
+  return prepare_sweep_kernel(sweep_fft_kernel<PREC, LS, SCALED, LAST, GatherIO<E>, R4>, K::SMEM);
 }
 
 using SweepFn = cudaError_t (*)(const void *, void *, const BatchItem *, int64_t, int, int, const uint4 *,
-                                cudaStream_t);
+                                const uint4 &, uint32_t, cudaStream_t);
 using SweepPrepFn = cudaError_t (*)();
 
-template <int PREC, bool SCALED, bool LAST, int... LSs>
+template <int PREC, bool SCALED, bool LAST, bool R4, int... LSs>
 struct SweepTable {
-  static constexpr SweepFn launch[] = {launch_sweep_one<PREC, LSs, SCALED, LAST>...};
-  static constexpr SweepPrepFn prepare[] = {prepare_sweep_one<PREC, LSs, SCALED, LAST>...};
+  static constexpr SweepFn launch[] = {launch_sweep_one<PREC, LSs, SCALED, LAST, R4>...};
+  static constexpr SweepPrepFn prepare[] = {prepare_sweep_one<PREC, LSs, SCALED, LAST, R4>...};
 };
 
 #define DSFFT_LS_LIST 7, 8, 9, 10, 11, 12
-template <int PREC>
+template <int PREC, bool R4>
 struct SweepSet {
-  using A = SweepTable<PREC, false, false, DSFFT_LS_LIST>;
-  using B = SweepTable<PREC, true, false, DSFFT_LS_LIST>;
-  using C = SweepTable<PREC, false, true, DSFFT_LS_LIST>;
-  using D = SweepTable<PREC, true, true, DSFFT_LS_LIST>;
+  using A = SweepTable<PREC, false, false, R4, DSFFT_LS_LIST>;
+  using B = SweepTable<PREC, true, false, R4, DSFFT_LS_LIST>;
+  using C = SweepTable<PREC, false, true, R4, DSFFT_LS_LIST>;
+  using D = SweepTable<PREC, true, true, R4, DSFFT_LS_LIST>;
   static SweepFn get(bool scaled, bool last, int ls) {
     const int i = ls - 7;
     if (!last) return scaled ? B::launch[i] : A::launch[i];
@@ -254,29 +314,66 @@ void sweep_split(int log2n, int *ls1, int *ls2) {
   *ls2 = log2n / 2;
 }
 
-cudaError_t prepare_sweeps(int prec, int log2n) {
+// Radix-4 plans: both sweeps hold whole radix-4 passes (sweep 1 also the
+// radix-2 pass of an odd log2 N), as balanced as LS in [7, 12] allows.
+void sweep_split4(int log2n, int *ls1, int *ls2) {
+  const int par = log2n & 1;
+  const int n4 = (log2n - par) / 2;
+  int a = (n4 + 1) / 2;
+  while (a > 0 && (par + 2 * a > 12 || 2 * (n4 - a) < 7)) --a;
+  while (par + 2 * a < 7 && 2 * (n4 - a) > 12) ++a;
+  *ls1 = par + 2 * a;
+  *ls2 = 2 * (n4 - a);
+}
+
+template <bool R4>
+static cudaError_t prepare_sweeps_impl(int prec, int log2n) {
   int ls1, ls2;
-  sweep_split(log2n, &ls1, &ls2);
+  if (R4) sweep_split4(log2n, &ls1, &ls2);
+  else sweep_split(log2n, &ls1, &ls2);
+  if (ls1 < 7 || ls1 > 12 || ls2 < 7 || ls2 > 12) return cudaErrorInvalidValue;
   for (int ls : {ls1, ls2}) {
-    cudaError_t e = prec == kFP32 ? SweepSet<kFP32>::prepare(ls)
-                    : prec == kFP16 ? SweepSet<kFP16>::prepare(ls) : SweepSet<kBF16>::prepare(ls);
+    cudaError_t e = prec == kFP32 ? SweepSet<kFP32, R4>::prepare(ls)
+                    : prec == kFP16 ? SweepSet<kFP16, R4>::prepare(ls) : SweepSet<kBF16, R4>::prepare(ls);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
 
-cudaError_t launch_sweeps(int prec, int log2n, bool scaled, const void *in, void *out, const BatchItem *items,
-                          int64_t batch, const uint4 *twp, cudaStream_t stream) {
+template <bool R4>
+static cudaError_t launch_sweeps_impl(int prec, int log2n, bool scaled, const void *in, void *out,
+                                      const BatchItem *items, int64_t batch, const uint4 *twp, const uint4 &r2e,
+                                      uint32_t sgn, cudaStream_t stream) {
   int ls1, ls2;
-  sweep_split(log2n, &ls1, &ls2);
+  if (R4) sweep_split4(log2n, &ls1, &ls2);
+  else sweep_split(log2n, &ls1, &ls2);
   if (ls1 < 7 || ls1 > 12 || ls2 < 7 || ls2 > 12) return cudaErrorInvalidValue;
   auto get = [&](bool last, int ls) {
-    return prec == kFP32 ? SweepSet<kFP32>::get(scaled, last, ls)
-           : prec == kFP16 ? SweepSet<kFP16>::get(scaled, last, ls) : SweepSet<kBF16>::get(scaled, last, ls);
+    return prec == kFP32 ? SweepSet<kFP32, R4>::get(scaled, last, ls)
+           : prec == kFP16 ? SweepSet<kFP16, R4>::get(scaled, last, ls) : SweepSet<kBF16, R4>::get(scaled, last, ls);
   };
-  cudaError_t e = get(false, ls1)(in, out, items, batch, log2n, 0, twp, stream);
+  cudaError_t e = get(false, ls1)(in, out, items, batch, log2n, 0, twp, r2e, sgn, stream);
   if (e != cudaSuccess) return e;
-  return get(true, ls2)(out, out, items, batch, log2n, ls1, twp, stream);
+  return get(true, ls2)(out, out, items, batch, log2n, ls1, twp, r2e, sgn, stream);
+}
+
+cudaError_t prepare_sweeps(int prec, int log2n) { return prepare_sweeps_impl<false>(prec, log2n); }
+
+cudaError_t launch_sweeps(int prec, int log2n, bool scaled, const void *in, void *out, const BatchItem *items,
+                          int64_t batch, const uint4 *twp, cudaStream_t stream) {
+  return launch_sweeps_impl<false>(prec, log2n, scaled, in, out, items, batch, twp, uint4{}, 0u, stream);
+}
+
+cudaError_t prepare_sweeps4(int prec, int log2n) { return prepare_sweeps_impl<true>(prec, log2n); }
+
+cudaError_t launch_sweeps4(int prec, int log2n, bool scaled, int inverse, const void *in, void *out,
+                           const BatchItem *items, int64_t batch, const uint4 *twp4, const uint4 &r2e,
+                           cudaStream_t stream) {
+  // sign operand of the +-i d3 terms: (s, -s), s = -1 forward, +1 inverse
+  const uint32_t sgn = prec == kFP32 ? (inverse ? 0x3F800000u : 0xBF800000u)
+                       : prec == kFP16 ? (inverse ? 0xBC003C00u : 0x3C00BC00u)
+                                       : (inverse ? 0xBF803F80u : 0x3F80BF80u);
+  return launch_sweeps_impl<true>(prec, log2n, scaled, in, out, items, batch, twp4, r2e, sgn, stream);
 }
 
 }  // namespace dsfft

@@ -81,7 +81,8 @@ def test_host_side_validation_without_gpu(lib):
     o.radix = 3
     assert lib.fft_plan_create(ctypes.byref(h), 1024, 0, 2, ctypes.byref(o)) == 1
     o.radix = 4
-    assert lib.fft_plan_create(ctypes.byref(h), 1 << 15, 0, 2, ctypes.byref(o)) == 3   # radix-4: N <= 2^14
+    o.variant = 3
+    assert lib.fft_plan_create(ctypes.byref(h), 1 << 15, 0, 2, ctypes.byref(o)) == 3   # radix-4 above 2^14: sweeps
     o.variant = 2
     assert lib.fft_plan_create(ctypes.byref(h), 1024, 0, 2, ctypes.byref(o)) == 3      # radix-4: fused wide only
     lib.fft_plan_opts_init(0, ctypes.byref(o))

@@ -85,3 +85,26 @@ def test_radix4_accuracy_vs_fp64(dsfft, prec, tol):
     ref = np.fft.fft(x, axis=-1) / (n if plan.scale_forward else 1)
     err = orc.rel_l2(y, ref)
     assert err < tol
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16", "bf16"])
+@pytest.mark.parametrize("log2n", [15, 16, 17, 18, 19, 20])
+def test_radix4_sweeps_bitexact(dsfft, prec, log2n):
+    """N > 2^14: two HBM sweeps of whole radix-4 passes (sweep 1 also holds
+    the radix-2 pass of an odd log2 N)."""
+    n = 1 << log2n
+    batch = 3 if log2n <= 17 else 1
+    x = signals.signal(300 + log2n, batch, n, prec)
+    plan = dsfft.Plan(n, prec, "dual_select", radix=4)
+    info = plan.info()
+    assert info["radix"] == 4 and info["kernel"] == 1 and info["launches"] == 2
+    for d in (-1, 1):
+        y = gpu_fft(plan, x, direction=d)
+        assert_bitexact(y, emulate_r4(plan, x, d), f"radix-4 sweeps {prec} N=2^{log2n} d={d}")
+
+
+def test_radix4_sweeps_largest(dsfft):
+    n = 1 << 22
+    x = signals.signal(5, 1, n, "fp16")
+    plan = dsfft.Plan(n, "fp16", "dual_select", radix=4)
+    assert_bitexact(gpu_fft(plan, x), emulate_r4(plan, x), "radix-4 fp16 N=2^22")
