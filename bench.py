@@ -311,26 +311,31 @@ def run_ours(args):
                             "rel_l2_vs_fp64": error_vs_fp64(p4, xs[l], ys[l], l, PRECISION, True)}
         del p4
 
-    # end to end: pinned host input -> device -> FFT -> host, every step
+    # end to end through the host-memory pipeline (fft_pipeline_exec): pinned
+    # host input -> device -> FFT -> host every step, 64 MiB chunks on 3
+    # streams so both copy directions and the kernels overlap
     e2e_steps = max(1, min(K, 3))
     host_in = {l: xs[l].cpu().pin_memory() for l in log2ns}
     host_out = {l: torch.empty_like(host_in[l]).pin_memory() for l in log2ns}
+    pipes = {l: dsfft.Pipeline(plans[l], max(1, (64 << 20) // (4 << l)), 3) for l in log2ns}
+    for l in log2ns:
+        pipes[l].exec(host_in[l], host_out[l], stream=stream)
     torch.cuda.synchronize()
     barrier(world)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
     for _ in range(e2e_steps):
         for l in log2ns:
-            xs[l].copy_(host_in[l], non_blocking=True)
-            plans[l].exec(xs[l], out=ys[l], stream=stream)
-            host_out[l].copy_(ys[l], non_blocking=True)
+            pipes[l].exec(host_in[l], host_out[l], stream=stream)
     b.record(stream)
     torch.cuda.synchronize()
     e2e_ms = allreduce_max(a.elapsed_time(b), world) / e2e_steps
     step_bytes = sum(2 * batch_for(l) * (2 << l) for l in log2ns)
     e2e = {"value": world * transforms_per_step / (e2e_ms / 1e3), "unit": "transforms/s",
            "h2d_bytes_per_step": step_bytes, "d2h_bytes_per_step": step_bytes, "ms_per_step": round(e2e_ms, 3),
-           "steps": e2e_steps}
+           "steps": e2e_steps, "api": "fft_pipeline_exec, pinned host buffers, 64 MiB chunks, 3 streams"}
+    for l in log2ns:
+        pipes[l].close()
 
     serve = None
     if not args.no_serve:

@@ -300,6 +300,30 @@ typedef struct fft_noalloc_item {
 
 DSFFT_API fft_status fft_exec_batch_noalloc(const fft_noalloc_item *items, int64_t count, void *stream);
 
+/* ---- Host-memory batches ------------------------------------------------------
+ * Not in the paper: a transfer pipeline for batches that live in host
+ * memory.  The batch is cut into chunks of `chunk_transforms` signals; chunk
+ * c is copied host -> device, transformed by the plan and copied back on
+ * internal stream c mod `depth`, so the two copy directions and the kernels
+ * of different chunks overlap.  The pipeline owns depth x 2 device staging
+ * buffers of one chunk each (allocated at creation) and references the plan,
+ * which must outlive it.  Host buffers: batch * N elements in the plan's
+ * layout; page-locked (cudaHostAlloc / cudaHostRegister) memory lets the
+ * copies run asynchronously, pageable memory works but serialises.
+ * host_in == host_out is allowed.  Calls on one pipeline must not overlap on
+ * the GPU (they share the staging buffers): order them on one stream. */
+typedef struct fft_pipeline fft_pipeline;
+
+/* depth in [1, 8]; FFT_ERR_OOM when the staging buffers do not fit. */
+DSFFT_API fft_status fft_pipeline_create(fft_pipeline **pipe, const fft_plan *plan, int64_t chunk_transforms,
+                                         int32_t depth);
+/* Asynchronous: the chunks start after work already queued on `stream`,
+ * and later work on `stream` waits for the last copy back. */
+DSFFT_API fft_status fft_pipeline_exec(fft_pipeline *pipe, const void *host_in, void *host_out, int64_t batch,
+                                       fft_direction dir, void *stream);
+/* Waits for the pipeline's streams, then frees it (NULL is accepted). */
+DSFFT_API fft_status fft_pipeline_destroy(fft_pipeline *pipe);
+
 /* ---- Serving loop with continuous batching --------------------------------
  * The paper has no serving layer: this is a front end that keeps requests of
  * mixed size, precision and direction flowing through the same kernels

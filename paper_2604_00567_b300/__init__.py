@@ -146,6 +146,9 @@ def lib():
             L.fft_batch_get_info.argtypes = [P, ctypes.POINTER(BatchInfo)]
             L.fft_batch_destroy.argtypes = [P]
             L.fft_exec_batch_noalloc.argtypes = [ctypes.POINTER(NoAllocItemC), i64, P]
+            L.fft_pipeline_create.argtypes = [ctypes.POINTER(P), P, i64, i32]
+            L.fft_pipeline_exec.argtypes = [P, P, P, i64, i32, P]
+            L.fft_pipeline_destroy.argtypes = [P]
             u64 = ctypes.c_uint64
             L.fft_server_opts_init.argtypes = [ctypes.POINTER(ServerOptsC)]
             L.fft_server_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(ServerOptsC)]
@@ -163,7 +166,8 @@ def lib():
             for name in ("fft_plan_opts_init", "fft_plan_create", "fft_plan_destroy", "fft_exec",
                          "fft_plan_get_table", "fft_plan_get_table4", "fft_plan_get_info", "fft_twiddle_fp64", "fft_batch_create",
                          "fft_batch_exec", "fft_batch_exec_graph", "fft_batch_get_info", "fft_batch_destroy",
-                         "fft_exec_batch_noalloc", "fft_server_opts_init", "fft_server_create",
+                         "fft_exec_batch_noalloc", "fft_pipeline_create", "fft_pipeline_exec",
+                         "fft_pipeline_destroy", "fft_server_opts_init", "fft_server_create",
                          "fft_server_prepare", "fft_server_submit", "fft_server_replay", "fft_server_poll",
                          "fft_server_wait", "fft_server_copy_out", "fft_server_release", "fft_server_drain",
                          "fft_server_get_stats", "fft_server_destroy"):
@@ -247,6 +251,20 @@ class Plan:
 
     def element_bytes(self) -> int:
         return 8 if self.precision == "fp32" else 4
+
+    def _check_tensor_shape(self, x):
+        """Signals in a contiguous tensor of the plan's layout (any device)."""
+        import torch
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        if self.precision == "fp32":
+            if x.dtype != torch.complex64 or x.shape[-1] != self.n:
+                raise ValueError(f"expected complex64 (..., {self.n}), got {x.dtype} {tuple(x.shape)}")
+            return x.numel() // self.n
+        want = torch.float16 if self.precision == "fp16" else torch.bfloat16
+        if x.dtype != want or x.shape[-2:] != (self.n, 2):
+            raise ValueError(f"expected {want} (..., {self.n}, 2), got {x.dtype} {tuple(x.shape)}")
+        return x.numel() // (2 * self.n)
 
     def _check_tensor(self, x, name):
         import torch
@@ -377,6 +395,43 @@ class Batch:
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             lib().fft_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Pipeline:
+    """Host-memory batches through a plan (``fft_pipeline_*``): chunks of
+    ``chunk_transforms`` signals are copied in, transformed and copied back on
+    ``depth`` streams so that copies and kernels overlap."""
+
+    def __init__(self, plan: Plan, chunk_transforms: int, depth: int = 3):
+        self.plan = plan
+        h = ctypes.c_void_p()
+        _check(lib().fft_pipeline_create(ctypes.byref(h), plan.handle, int(chunk_transforms), int(depth)),
+               "fft_pipeline_create")
+        self._h = h
+
+    def exec(self, host_in, host_out, direction: int = FORWARD, stream=None):
+        """``host_in``/``host_out``: CPU tensors (pinned for overlap) in the
+        plan's layout."""
+        if host_in.is_cuda or host_out.is_cuda:
+            raise ValueError("pipeline buffers are host tensors")
+        batch = self.plan._check_tensor_shape(host_in)
+        if self.plan._check_tensor_shape(host_out) != batch:
+            raise ValueError("host_out must match host_in")
+        _check(lib().fft_pipeline_exec(self._h, ctypes.c_void_p(host_in.data_ptr()),
+                                       ctypes.c_void_p(host_out.data_ptr()), batch, int(direction),
+                                       _stream_handle(stream)), "fft_pipeline_exec")
+        return host_out
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().fft_pipeline_destroy(self._h)
             self._h = None
 
     def __del__(self):
