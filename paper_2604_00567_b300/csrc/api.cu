@@ -87,7 +87,7 @@ bool variant_valid(int prec, int log2n, int v) {
 int default_variant(int prec, int log2n) {
   if (log2n <= kFusedMaxLog2N) {
     const bool narrow = prec == kFP32 ? (log2n >= 5 && log2n <= 7)
-                                      : ((log2n >= 5 && log2n <= 8) || log2n == 12);
+                                      : (log2n >= 5 && log2n <= 8);
     return narrow && fused_has_narrow(prec, log2n) ? FFT_VARIANT_FUSED_NARROW : FFT_VARIANT_FUSED_WIDE;
   }
   if (log2n == 15 || (log2n == 16 && prec != kFP32)) return FFT_VARIANT_CLUSTER;

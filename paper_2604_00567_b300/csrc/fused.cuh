@@ -77,9 +77,33 @@ struct Fused {
   }
   static_assert(BT == 0 || T <= BT, "a transform fits the block");
 
-  // rho radix-2 passes starting at pass P on the registers of one thread.
-  // tw0(i) returns per-pass entry i for the first stage (the same for every
-  // thread): the constant bank or the global table.
+  // rho radix-2 passes starting at pass P on the registers of one thread,
+  // in depth-first order: pass I on a block of 2^(rho - I) registers, then
+  // each half of the block through the remaining passes (the halves are
+  // independent after pass I).  Every butterfly keeps its operands and
+  // twiddle, so the result is that of the pass-by-pass order; the order
+  // keeps fewer twiddles live and lets the loads of one block overlap the
+  // arithmetic of the previous one.  tw0(i) returns per-pass entry i for the
+  // first stage (the same for every thread): the constant bank or the global
+  // table.
+  template <int P, int RHO, int CI, int I, int QTOP, class TW0>
+  static __device__ __forceinline__ void dfs(E (&v)[R], int j, const uint4 *__restrict__ tw, const TW0 &tw0) {
+    constexpr int C = R >> RHO;
+    constexpr int half = 1 << (RHO - 1 - I);
+    constexpr int ql = bitrev(QTOP >> (RHO - I), I);   // pass P+I, j_full = j + ql 2^P
+    uint4 e;
+    if constexpr (P == 0) e = tw0(((1 << I) - 1) + ql);
+    else e = tw_load<PREC>(tw, ((1 << (P + I)) - 1) + j + (ql << P));
+    static_for<0, half>([&](auto qh_) {
+      constexpr int q = QTOP | decltype(qh_)::value;
+      Bfly<PREC, SCALED>::run(v[CI + q * C], v[CI + (q + half) * C], e);
+    });
+    if constexpr (I + 1 < RHO) {
+      dfs<P, RHO, CI, I + 1, QTOP>(v, j, tw, tw0);
+      dfs<P, RHO, CI, I + 1, QTOP + half>(v, j, tw, tw0);
+    }
+  }
+
   template <int P, int RHO, class TW0>
   static __device__ __forceinline__ void compute(E (&v)[R], int tid, const uint4 *__restrict__ tw, const TW0 &tw0) {
     constexpr int C = R >> RHO;   // independent groups per thread
@@ -87,23 +111,7 @@ struct Fused {
       constexpr int c = decltype(c_)::value;
       const int g = tid + c * T;
       const int j = g & ((1 << P) - 1);
-      static_for<0, RHO>([&](auto i_) {
-        constexpr int i = decltype(i_)::value;
-        constexpr int half = 1 << (RHO - 1 - i);
-        static_for<0, (1 << i)>([&](auto ql_) {
-          constexpr int ql = decltype(ql_)::value;
-          // pass P+i, j_full = j + ql 2^P; the first stage (j = 0) reads the
-          // constant bank
-          uint4 e;
-          if constexpr (P == 0) e = tw0(((1 << i) - 1) + ql);
-          else e = tw_load<PREC>(tw, ((1 << (P + i)) - 1) + j + (ql << P));
-          constexpr int qtop = bitrev(ql, i) << (RHO - i);
-          static_for<0, half>([&](auto qh_) {
-            constexpr int q = qtop | decltype(qh_)::value;
-            Bfly<PREC, SCALED>::run(v[c + q * C], v[c + (q + half) * C], e);
-          });
-        });
-      });
+      dfs<P, RHO, c, 0, 0>(v, j, tw, tw0);
     });
   }
 

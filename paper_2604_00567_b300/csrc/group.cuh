@@ -26,7 +26,29 @@ struct GroupPasses {
   static constexpr int T = M / R;
 
   // tw0(i): per-pass entry i for the first register stage when P0 = 0 (the
-  // same for every thread: the constant bank).
+  // same for every thread: the constant bank).  Depth-first order over the
+  // stage's passes (as in fused.cuh): pass I on a block of registers, then
+  // its two halves.
+  template <int PL, int RHO, int CI, int I, int QTOP, class TW0>
+  static __device__ __forceinline__ void dfs(E (&v)[R], int jg, int jloc, const uint4 *__restrict__ twp,
+                                             const TW0 &tw0) {
+    constexpr int C = R >> RHO;
+    constexpr int half = 1 << (RHO - 1 - I);
+    constexpr int ql = bitrev(QTOP >> (RHO - I), I);
+    constexpr int p = P0 + PL + I;                     // global pass
+    uint4 e;
+    if constexpr (P0 == 0 && PL == 0) e = tw0(((1 << I) - 1) + ql);
+    else e = tw_load<PREC>(twp, ((1 << p) - 1) + jg + (jloc << P0) + (ql << (PL + P0)));
+    static_for<0, half>([&](auto qh_) {
+      constexpr int q = QTOP | decltype(qh_)::value;
+      Bfly<PREC, SCALED>::run(v[CI + q * C], v[CI + (q + half) * C], e);
+    });
+    if constexpr (I + 1 < RHO) {
+      dfs<PL, RHO, CI, I + 1, QTOP>(v, jg, jloc, twp, tw0);
+      dfs<PL, RHO, CI, I + 1, QTOP + half>(v, jg, jloc, twp, tw0);
+    }
+  }
+
   template <int PL, int RHO, class TW0>
   static __device__ __forceinline__ void compute(E (&v)[R], int tid, int jg, const uint4 *__restrict__ twp,
                                                  const TW0 &tw0) {
@@ -34,27 +56,11 @@ struct GroupPasses {
     static_for<0, C>([&](auto c_) {
       constexpr int c = decltype(c_)::value;
       // keep each group's twiddle loads next to their use: hoisting all
-      // C (2^RHO - 1) 16-byte entries ahead would exhaust the registers
+      // C (2^RHO - 1) entries ahead would exhaust the registers
       if constexpr (c > 0) asm volatile("" ::: "memory");
       const int gl = tid + c * T;
       const int jloc = gl & ((1 << PL) - 1);
-      static_for<0, RHO>([&](auto i_) {
-        constexpr int i = decltype(i_)::value;
-        constexpr int half = 1 << (RHO - 1 - i);
-        constexpr int p = P0 + PL + i;                     // global pass
-        const int tp = ((1 << p) - 1) + jg + (jloc << P0);
-        static_for<0, (1 << i)>([&](auto ql_) {
-          constexpr int ql = decltype(ql_)::value;
-          uint4 e;
-          if constexpr (P0 == 0 && PL == 0) e = tw0(((1 << i) - 1) + ql);
-          else e = tw_load<PREC>(twp, tp + (ql << (PL + P0)));
-          constexpr int qtop = bitrev(ql, i) << (RHO - i);
-          static_for<0, half>([&](auto qh_) {
-            constexpr int q = qtop | decltype(qh_)::value;
-            Bfly<PREC, SCALED>::run(v[c + q * C], v[c + (q + half) * C], e);
-          });
-        });
-      });
+      dfs<PL, RHO, c, 0, 0>(v, jg, jloc, twp, tw0);
     });
   }
 
