@@ -14,6 +14,8 @@ Also reported on the same JSON line:
                  error vs an FP64 FFT (numpy) on sampled signals, per N;
   fp32_plain   : the FP32 form (no scaling) on the same bytes per N;
   radix4_fp16  : radix-4 dual-select plans (N <= 2^14) on the same FP16 batches;
+  batch_c3     : a mixed batch of 4096 transforms (N 2^6..2^16, FP32/FP16) as
+                 one graph-replayed fft_batch;
   e2e          : the same metric with the input copied from pinned host
                  memory and the output copied back inside the timed region;
   cpu_baseline : the CPU oracle (op-by-op emulation) on a bounded sample;
@@ -337,6 +339,8 @@ def run_ours(args):
     for l in log2ns:
         pipes[l].close()
 
+    c3 = batch_c3()
+
     serve = None
     if not args.no_serve:
         serve = serve_measure(args.serve_seconds)
@@ -355,7 +359,7 @@ def run_ours(args):
                        "precision": PRECISION, "factorization": FACTORIZATION,
                        "input": "re/im i.i.d. uniform[-1,1], torch.Generator seeded",
                        "l2": "inputs 1 GiB per launch > 126 MB L2; no flush", "parallelism": f"replicas{world}"},
-            "roofline": roofline, "per_n": per_n, "fp32_plain": fp32, "radix4_fp16": radix4, "e2e": e2e,
+            "roofline": roofline, "per_n": per_n, "fp32_plain": fp32, "radix4_fp16": radix4, "batch_c3": c3, "e2e": e2e,
             "gpu_launches": K * sum(plans[l].info()["launches"] for l in log2ns),
             "clocks": clocks, "cpu_baseline": cpu, "serve": serve,
         }
@@ -363,6 +367,62 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+def batch_c3(steps: int = 10, count: int = 4096, seed: int = 1):
+    """Mixed batch (config C3): `count` forward dual-select transforms with
+    N = 2^e, e ~ U{6..16}, precision FP32 or FP16 with probability 1/2
+    (seeded), each with its own input/output rows, run as one fft_batch
+    (one persistent launch for N <= 2^14 plus one launch per larger group)
+    replayed as a CUDA graph.  For context also the same work as one
+    fft_exec per (N, precision) group."""
+    import torch
+    import paper_2604_00567_b300 as dsfft
+    from paper_2604_00567_b300 import signals
+    rng = np.random.default_rng(seed)
+    es = rng.integers(6, 17, count)
+    fp32 = rng.random(count) < 0.5
+    groups = {}
+    for i in range(count):
+        groups.setdefault((int(es[i]), "fp32" if fp32[i] else "fp16"), []).append(i)
+    xs, ys, items, nbytes = {}, {}, [], 0
+    for (e, prec), idx in sorted(groups.items()):
+        xs[(e, prec)] = signals.device_signal(len(idx), 1 << e, prec, seed=seed * 100 + e)
+        ys[(e, prec)] = torch.empty_like(xs[(e, prec)])
+        for r in range(len(idx)):
+            items.append((1 << e, prec, FACTORIZATION, -1, xs[(e, prec)][r:r + 1], ys[(e, prec)][r:r + 1]))
+        nbytes += 2 * len(idx) * ((8 if prec == "fp32" else 4) << e)
+    b = dsfft.Batch(items)
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        b.exec_graph()
+    a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        b.exec_graph()
+    z.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(z) / steps
+    info = b.info()
+    plans = {k: dsfft.Plan(1 << k[0], k[1], FACTORIZATION) for k in groups}
+    for _ in range(3):
+        for k, p in plans.items():
+            p.exec(xs[k], out=ys[k])
+    a.record(stream)
+    for _ in range(steps):
+        for k, p in plans.items():
+            p.exec(xs[k], out=ys[k])
+    z.record(stream)
+    torch.cuda.synchronize()
+    ms_grouped = a.elapsed_time(z) / steps
+    b.close()
+    return {"config": f"C3: {count} transforms, N = 2^U{{6..16}}, FP32/FP16 p=0.5 (seed {seed}), dual_select "
+                      "forward, own buffers per transform, one fft_batch replayed as a CUDA graph",
+            "ms_per_exec": round(ms, 4), "transforms_per_s": count / (ms / 1e3),
+            "algorithmic_GB_per_s": round(nbytes / (ms / 1e3) / 1e9, 1), "launches_per_exec": info["launches"],
+            "persistent_tiles": info["tiles"],
+            "grouped_exec_ms": round(ms_grouped, 4), "grouped_exec_launches": len(plans)}
 
 
 # ---------------------------------------------------------------------------

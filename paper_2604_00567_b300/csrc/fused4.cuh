@@ -56,6 +56,43 @@ struct Fused4 : Fused<PREC, LOG2N, LOG2R, SCALED, BT> {
   static constexpr bool MULTI_STAGE = r4_stage_levels(LOG2N, LOG2R, 0) < LOG2N;
   static_assert(!MULTI_STAGE || Base::SMEM > 0, "an exchange buffer whenever there are several stages");
 
+  // Radix-4 pass at stage-local level I on the block of registers starting
+  // at QTOP (2^(RHO - I) registers), then its four quarter blocks through the
+  // remaining passes (they are independent after it): depth-first, as in
+  // fused.cuh.
+  template <int P, int RHO, int CI, int I, int QTOP>
+  static __device__ __forceinline__ void dfs4(E (&v)[R], int j, const uint4 *__restrict__ tw, const Stage0R4 &tw0,
+                                              S sgn) {
+    constexpr int C = R >> RHO;
+    constexpr int lvl = P + I;
+    constexpr int L = 1 << lvl;
+    constexpr int Q = 1 << (RHO - I - 2);
+    constexpr int ql = bitrev(QTOP >> (RHO - I), I);
+    uint4 e1, e2, e3;
+    if constexpr (P == 0) {
+      constexpr int o = (int)r4_offset(lvl, PAR) + ql;
+      e1 = tw0.e[o];
+      e2 = tw0.e[o + L];
+      e3 = tw0.e[o + 2 * L];
+    } else {
+      const int at = (int)r4_offset(lvl, PAR) + j + (ql << P);
+      e1 = tw_load<PREC>(tw, at);
+      e2 = tw_load<PREC>(tw, at + L);
+      e3 = tw_load<PREC>(tw, at + 2 * L);
+    }
+    static_for<0, Q>([&](auto qh_) {
+      constexpr int q0 = QTOP | decltype(qh_)::value;
+      Bfly4<PREC, SCALED>::run(v[CI + q0 * C], v[CI + (q0 + Q) * C], v[CI + (q0 + 2 * Q) * C],
+                               v[CI + (q0 + 3 * Q) * C], e1, e2, e3, sgn);
+    });
+    if constexpr (I + 2 < RHO) {
+      dfs4<P, RHO, CI, I + 2, QTOP>(v, j, tw, tw0, sgn);
+      dfs4<P, RHO, CI, I + 2, QTOP + Q>(v, j, tw, tw0, sgn);
+      dfs4<P, RHO, CI, I + 2, QTOP + 2 * Q>(v, j, tw, tw0, sgn);
+      dfs4<P, RHO, CI, I + 2, QTOP + 3 * Q>(v, j, tw, tw0, sgn);
+    }
+  }
+
   template <int P, int RHO>
   static __device__ __forceinline__ void compute(E (&v)[R], int tid, const uint4 *__restrict__ tw,
                                                  const Stage0R4 &tw0, S sgn) {
@@ -65,7 +102,6 @@ struct Fused4 : Fused<PREC, LOG2N, LOG2R, SCALED, BT> {
     static_assert((RHO - I0) % 2 == 0, "a stage holds whole radix-4 passes");
     static_for<0, C>([&](auto c_) {
       constexpr int c = decltype(c_)::value;
-      if constexpr (c > 0) asm volatile("" ::: "memory");
       const int g = tid + c * T;
       const int j = g & ((1 << P) - 1);
       if constexpr (R2) {
@@ -74,34 +110,13 @@ struct Fused4 : Fused<PREC, LOG2N, LOG2R, SCALED, BT> {
           constexpr int q = decltype(qh_)::value;
           Bfly<PREC, SCALED>::run(v[c + q * C], v[c + (q + half) * C], tw0.r2);
         });
+        if constexpr (RHO > 1) {
+          dfs4<P, RHO, c, 1, 0>(v, j, tw, tw0, sgn);
+          dfs4<P, RHO, c, 1, half>(v, j, tw, tw0, sgn);
+        }
+      } else {
+        dfs4<P, RHO, c, 0, 0>(v, j, tw, tw0, sgn);
       }
-      static_for<0, (RHO - I0) / 2>([&](auto k_) {
-        constexpr int i = I0 + 2 * decltype(k_)::value;   // stage-local level of this radix-4 pass
-        constexpr int lvl = P + i;
-        constexpr int L = 1 << lvl;
-        constexpr int Q = 1 << (RHO - i - 2);
-        const int base = (int)r4_offset(lvl, PAR) + j;
-        static_for<0, (1 << i)>([&](auto ql_) {
-          constexpr int ql = decltype(ql_)::value;
-          uint4 e1, e2, e3;
-          if constexpr (P == 0) {
-            constexpr int o = (int)r4_offset(lvl, PAR) + ql;
-            e1 = tw0.e[o];
-            e2 = tw0.e[o + L];
-            e3 = tw0.e[o + 2 * L];
-          } else {
-            e1 = tw_load<PREC>(tw, base + (ql << P));
-            e2 = tw_load<PREC>(tw, base + (ql << P) + L);
-            e3 = tw_load<PREC>(tw, base + (ql << P) + 2 * L);
-          }
-          constexpr int qtop = bitrev(ql, i) << (RHO - i);
-          static_for<0, Q>([&](auto qh_) {
-            constexpr int q0 = qtop | decltype(qh_)::value;
-            Bfly4<PREC, SCALED>::run(v[c + q0 * C], v[c + (q0 + Q) * C], v[c + (q0 + 2 * Q) * C],
-                                     v[c + (q0 + 3 * Q) * C], e1, e2, e3, sgn);
-          });
-        });
-      });
     });
   }
 
