@@ -439,7 +439,8 @@ def serve_trace(seconds: float, rate: float, seed: int = 2):
     return arrivals, log2n, signals_, fp32
 
 
-def serve_measure(seconds: float = 1.0, rate: float = 20000.0, budget: int = 40_000_000_000):
+def serve_measure(seconds: float = 1.0, rate: float = 20000.0, budget: int = 40_000_000_000,
+                  max_tick_bytes: int = 1 << 30):
     """Serving loop under the arrival trace: inputs resident on the device
     (read from per-precision pools), outputs in the server's 40 GB arena
     (freed at completion).  Latency = completion seen by the scheduler -
@@ -451,7 +452,7 @@ def serve_measure(seconds: float = 1.0, rate: float = 20000.0, budget: int = 40_
     pools = {"fp32": signals.device_signal(256, 1 << 18, "fp32", seed=21),
              "fp16": signals.device_signal(256, 1 << 18, "fp16", seed=22)}
     torch.cuda.synchronize()
-    srv = dsfft.Server(memory_budget=budget, release_on_complete=True)
+    srv = dsfft.Server(memory_budget=budget, release_on_complete=True, max_tick_bytes=max_tick_bytes)
     try:
         reqs = []
         for k in range(len(arrivals)):
@@ -482,7 +483,8 @@ def serve_measure(seconds: float = 1.0, rate: float = 20000.0, budget: int = 40_
     return {
         "config": "C5: Poisson %.0f req/s for %.1f s (seed 2), U{1..256} signals, N = 2^U{8..18}, "
                   "FP32/FP16 p=0.5 (dual_select), inputs resident on the device, 40 GB arena, "
-                  "outputs freed at completion" % (rate, seconds),
+                  "outputs freed at completion, ticks of at most %d MiB of output" % (rate, seconds,
+                                                                                max_tick_bytes >> 20),
         "requests": len(arrivals), "completed_ok": len(ok),
         "p50_ms": round(float(np.percentile(lat_ms, 50)), 3), "p99_ms": round(float(np.percentile(lat_ms, 99)), 3),
         "max_ms": round(float(lat_ms.max()), 3), "mean_ms": round(float(lat_ms.mean()), 3),

@@ -357,7 +357,12 @@ typedef struct fft_server_opts {
     int32_t autotune;             /* plans created with autotune (0/1) */
     int32_t release_on_complete;  /* free the output slot at completion: the
                                      output pointer is then not usable (0/1) */
-    int32_t reserved[4];          /* must be zero */
+    int64_t max_tick_bytes;       /* output bytes per tick at most (the first
+                                     request of a tick is always taken); 0 =
+                                     no limit (default).  Smaller ticks finish
+                                     sooner, which shortens the wait of the
+                                     requests that arrive while they run. */
+    int32_t reserved[2];          /* must be zero */
 } fft_server_opts;
 
 typedef struct fft_request {

@@ -89,7 +89,7 @@ class ServerOptsC(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("max_ticks_in_flight", ctypes.c_int32),
                 ("memory_budget", ctypes.c_uint64), ("max_tick_transforms", ctypes.c_int64),
                 ("autotune", ctypes.c_int32), ("release_on_complete", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("max_tick_bytes", ctypes.c_int64), ("reserved", ctypes.c_int32 * 2)]
 
 
 class RequestC(ctypes.Structure):
@@ -455,7 +455,7 @@ class Server:
 
     def __init__(self, memory_budget: int = 40_000_000_000, max_ticks_in_flight: int = 2,
                  max_tick_transforms: int = 1 << 20, device: int | None = None, autotune: bool = False,
-                 release_on_complete: bool = False):
+                 release_on_complete: bool = False, max_tick_bytes: int = 0):
         L = lib()
         o = ServerOptsC()
         _check(L.fft_server_opts_init(ctypes.byref(o)), "fft_server_opts_init")
@@ -464,6 +464,7 @@ class Server:
         o.max_tick_transforms = int(max_tick_transforms)
         o.autotune = 1 if autotune else 0
         o.release_on_complete = 1 if release_on_complete else 0
+        o.max_tick_bytes = int(max_tick_bytes)
         if device is not None:
             o.device = int(device)
         h = ctypes.c_void_p()

@@ -305,10 +305,12 @@ void scheduler(fft_server *s) {
     if (free_slot >= 0 && !s->admitted.empty()) {
       Slot &sl = s->slots[free_slot];
       sl.reqs.clear();
-      int64_t small_count = 0;
+      int64_t small_count = 0, tick_bytes = 0;
       while (!s->admitted.empty()) {
         Request *r = s->admitted.front();
         if (small_request(r) && small_count + r->req.count > s->opts.max_tick_transforms) break;
+        if (s->opts.max_tick_bytes > 0 && !sl.reqs.empty() && tick_bytes + r->bytes > s->opts.max_tick_bytes) break;
+        tick_bytes += r->bytes;
         if (small_request(r)) small_count += r->req.count;
         s->admitted.pop_front();
         r->state = kLaunched;
@@ -425,6 +427,7 @@ fft_status fft_server_create(fft_server **server, const fft_server_opts *opts_in
     return FFT_ERR_INVALID_ARG;
   if ((o.autotune != 0 && o.autotune != 1) || (o.release_on_complete != 0 && o.release_on_complete != 1))
     return FFT_ERR_INVALID_ARG;
+  if (o.max_tick_bytes < 0) return FFT_ERR_INVALID_ARG;
 
   int prev = -1;
   cudaError_t e = cudaGetDevice(&prev);

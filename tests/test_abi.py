@@ -146,11 +146,13 @@ def test_server_validation_without_gpu(lib):
     assert lib.fft_server_opts_init(ctypes.byref(o)) == 0
     assert o.device == -1 and o.max_ticks_in_flight == 2 and o.memory_budget == 40_000_000_000
     assert o.max_tick_transforms == 1 << 20 and o.autotune == 0 and o.release_on_complete == 0
+    assert o.max_tick_bytes == 0
     assert lib.fft_server_opts_init(None) == 1
     h = ctypes.c_void_p()
     assert lib.fft_server_create(None, ctypes.byref(o)) == 1
     for field, bad in (("max_ticks_in_flight", 0), ("max_ticks_in_flight", 9), ("memory_budget", 0),
-                       ("max_tick_transforms", 0), ("autotune", 2), ("release_on_complete", 3)):
+                       ("max_tick_transforms", 0), ("autotune", 2), ("release_on_complete", 3),
+                       ("max_tick_bytes", -1)):
         lib.fft_server_opts_init(ctypes.byref(o))
         setattr(o, field, bad)
         assert lib.fft_server_create(ctypes.byref(h), ctypes.byref(o)) == 1, field

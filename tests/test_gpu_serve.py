@@ -206,3 +206,21 @@ def test_replay_poisson_trace(dsfft):
     lat = np.array([c["t_done_ns"] - c["t_submit_ns"] for c in done])
     assert np.all(lat > 0)
     assert len({c["tick"] for c in done}) < count
+
+
+def test_tick_byte_limit(dsfft):
+    """max_tick_bytes splits the admitted requests into ticks of at most that
+    many output bytes (a single larger request still forms its own tick)."""
+    n, prec = 1 << 14, "fp32"                 # 128 KiB per signal
+    xs = [signals.device_signal(8, n, prec, seed=k) for k in range(10)]   # 1 MiB each
+    with dsfft.Server(memory_budget=64 << 20, max_ticks_in_flight=1, max_tick_bytes=2 << 20) as srv:
+        ts = [srv.submit(x, n, prec) for x in xs]
+        cs = [srv.wait(t, 30.0) for t in ts]
+        for t in ts:
+            srv.release(t)
+    ticks = {}
+    for c in cs:
+        assert c["status"] == 0
+        ticks.setdefault(c["tick"], 0)
+        ticks[c["tick"]] += c["bytes"]
+    assert all(b <= 2 << 20 for b in ticks.values()) and len(ticks) >= 5
