@@ -400,7 +400,7 @@ fft_status fft_plan_create(fft_plan **plan, int64_t n, fft_precision prec, fft_f
 
   const size_t entries = (size_t)(n / 2);
   // per-pass tables hold the compact 8-byte entries for FP16/BF16
-  const int compact = prec == kFP32 ? 0 : 1;
+  const int compact = (int)prec == kFP32 ? 0 : 1;
   const size_t tw_bytes = compact ? sizeof(uint2) : sizeof(uint4);
   int *counts = nullptr;
   uint4 *head = nullptr;      // 16-byte forms of the first-stage entries: [dir][radix 2/4][31]
