@@ -374,7 +374,7 @@ def run_ours(args):
 
 # ---------------------------------------------------------------------------
 def batch_c3(steps: int = 10, count: int = 4096, seed: int = 1):
-    """Mixed batch (config C3): `count` forward dual-select transforms with
+    """Mixed batch: `count` forward dual-select transforms with
     N = 2^e, e ~ U{6..16}, precision FP32 or FP16 with probability 1/2
     (seeded), each with its own input/output rows, run as one fft_batch
     (one persistent launch for N <= 2^14 plus one launch per larger group)
@@ -420,7 +420,7 @@ def batch_c3(steps: int = 10, count: int = 4096, seed: int = 1):
     torch.cuda.synchronize()
     ms_grouped = a.elapsed_time(z) / steps
     b.close()
-    return {"config": f"C3: {count} transforms, N = 2^U{{6..16}}, FP32/FP16 p=0.5 (seed {seed}), dual_select "
+    return {"config": f"mixed batch: {count} transforms, N = 2^U{{6..16}}, FP32/FP16 p=0.5 (seed {seed}), dual_select "
                       "forward, own buffers per transform, one fft_batch replayed as a CUDA graph",
             "ms_per_exec": round(ms, 4), "transforms_per_s": count / (ms / 1e3),
             "algorithmic_GB_per_s": round(nbytes / (ms / 1e3) / 1e9, 1), "launches_per_exec": info["launches"],
@@ -484,7 +484,7 @@ def serve_measure(seconds: float = 1.0, rate: float = 20000.0, budget: int = 40_
     transforms = int(sum(int(sig[c["tag"]]) for c in ok))
     payload = int(sum(2 * c["bytes"] for c in ok))
     return {
-        "config": "C5: Poisson %.0f req/s for %.1f s (seed 2), U{1..256} signals, N = 2^U{8..18}, "
+        "config": "open-loop Poisson trace %.0f req/s for %.1f s (seed 2), U{1..256} signals, N = 2^U{8..18}, "
                   "FP32/FP16 p=0.5 (dual_select), inputs resident on the device, 40 GB arena, "
                   "outputs freed at completion, ticks of at most %d MiB of output" % (rate, seconds,
                                                                                 max_tick_bytes >> 20),

@@ -55,7 +55,7 @@ typedef enum fft_status {
     FFT_OK = 0,
     FFT_ERR_INVALID_ARG = 1,   /* null pointer, bad enum, negative batch */
     FFT_ERR_INVALID_SIZE = 2,  /* N not a power of two or outside [2, 2^24] */
-    FFT_ERR_UNSUPPORTED = 3,   /* valid request this build cannot run */
+    FFT_ERR_UNSUPPORTED = 3,   /* valid request the library does not implement */
     FFT_ERR_OOM = 4,           /* device allocation failed */
     FFT_ERR_CUDA = 5,          /* a CUDA runtime call or launch failed */
     FFT_ERR_TIMEOUT = 6        /* a bounded device-side wait gave up */
