@@ -191,8 +191,8 @@ cudaError_t autotune_plan(fft_plan *p) {
   int best = -1;
   float best_ms = 0.f;
   do {
-    if ((e = cudaMalloc(&in, tbytes * batch)) != cudaSuccess) break;
-    if ((e = cudaMalloc(&out, tbytes * batch)) != cudaSuccess) break;
+    if ((e = device_alloc(&in, tbytes * batch)) != cudaSuccess) break;
+    if ((e = device_alloc(&out, tbytes * batch)) != cudaSuccess) break;
     if ((e = cudaMemset(in, 0x11, tbytes * batch)) != cudaSuccess) break;   // finite, normal values
     if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) break;
     if ((e = cudaEventCreate(&a)) != cudaSuccess) break;
@@ -258,6 +258,25 @@ bool dsfft::plan_view(const fft_plan *p, PlanView *v) {
 }
 
 void dsfft::set_last_error(const char *msg) { snprintf(g_last_error, sizeof g_last_error, "%s", msg); }
+
+cudaError_t dsfft::device_alloc(void **ptr, size_t bytes) {
+  static std::mutex mu;
+  static std::string seen;
+  static long count = 0;
+  const char *v = getenv("DSFFT_FAULT_ALLOC");
+  if (v && *v) {
+    std::lock_guard<std::mutex> lk(mu);
+    if (seen != v) {
+      seen = v;
+      count = 0;
+    }
+    if (++count == atol(v)) {
+      *ptr = nullptr;
+      return cudaErrorMemoryAllocation;
+    }
+  }
+  return cudaMalloc(ptr, bytes);
+}
 
 extern "C" {
 
@@ -408,12 +427,12 @@ fft_status fft_plan_create(fft_plan **plan, int64_t n, fft_precision prec, fft_f
   fft_status status = FFT_OK;
   int host_counts[2] = {0, 0};
   do {
-    if ((e = cudaMalloc(&p->table[0], entries * sizeof(uint4))) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc table"); break; }
-    if ((e = cudaMalloc(&p->table[1], entries * sizeof(uint4))) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc table"); break; }
-    if ((e = cudaMalloc(&p->twp[0], (size_t)(n - 1) * tw_bytes)) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc table"); break; }
-    if ((e = cudaMalloc(&p->twp[1], (size_t)(n - 1) * tw_bytes)) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc table"); break; }
-    if ((e = cudaMalloc(&counts, 2 * sizeof(int))) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc counts"); break; }
-    if ((e = cudaMalloc(&head, 4 * 31 * sizeof(uint4))) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc"); break; }
+    if ((e = device_alloc(&p->table[0], entries * sizeof(uint4))) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc table"); break; }
+    if ((e = device_alloc(&p->table[1], entries * sizeof(uint4))) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc table"); break; }
+    if ((e = device_alloc(&p->twp[0], (size_t)(n - 1) * tw_bytes)) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc table"); break; }
+    if ((e = device_alloc(&p->twp[1], (size_t)(n - 1) * tw_bytes)) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc table"); break; }
+    if ((e = device_alloc(&counts, 2 * sizeof(int))) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc counts"); break; }
+    if ((e = device_alloc(&head, 4 * 31 * sizeof(uint4))) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc"); break; }
     if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) { status = cuda_fail(e, "stream"); break; }
     if ((e = cudaMemsetAsync(counts, 0, 2 * sizeof(int), st)) != cudaSuccess) { status = cuda_fail(e, "memset"); break; }
     if ((e = launch_build_table(log2n, n / 2, fac, opts.lf_eps, prec, 0, p->scale[0] ? 0.5 : 1.0, p->table[0], counts, st)) != cudaSuccess) { status = cuda_fail(e, "table build"); break; }
@@ -429,8 +448,8 @@ fft_status fft_plan_create(fft_plan **plan, int64_t n, fft_precision prec, fft_f
     if (radix == 4) {
       const int64_t c4 = 3 * n / 4, p4 = n - 1 - (log2n & 1);
       for (int d = 0; d < 2 && e == cudaSuccess; ++d) {
-        if ((e = cudaMalloc(&p->table4[d], (size_t)(c4 > 0 ? c4 : 1) * sizeof(uint4))) != cudaSuccess) break;
-        if ((e = cudaMalloc(&p->twp4[d], (size_t)(p4 > 0 ? p4 : 1) * tw_bytes)) != cudaSuccess) break;
+        if ((e = device_alloc(&p->table4[d], (size_t)(c4 > 0 ? c4 : 1) * sizeof(uint4))) != cudaSuccess) break;
+        if ((e = device_alloc(&p->twp4[d], (size_t)(p4 > 0 ? p4 : 1) * tw_bytes)) != cudaSuccess) break;
         if ((e = launch_build_table(log2n, c4, fac, opts.lf_eps, prec, d, p->scale[d] ? 0.25 : 1.0, p->table4[d],
                                     nullptr, st)) != cudaSuccess)
           break;
@@ -585,9 +604,9 @@ fft_status fft_twiddle_fp64(int64_t n, fft_factorization fac, double lf_eps, dou
   fft_status status = FFT_OK;
   cudaError_t e;
   do {
-    if ((e = cudaMalloc(&t, h * sizeof(double))) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc"); break; }
-    if ((e = cudaMalloc(&m, h * sizeof(double))) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc"); break; }
-    if ((e = cudaMalloc(&path, h * sizeof(int))) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc"); break; }
+    if ((e = device_alloc(&t, h * sizeof(double))) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc"); break; }
+    if ((e = device_alloc(&m, h * sizeof(double))) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc"); break; }
+    if ((e = device_alloc(&path, h * sizeof(int))) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc"); break; }
     if ((e = launch_fp64_table(log2n, fac, lf_eps, t, m, path, nullptr)) != cudaSuccess) { status = cuda_fail(e, "fp64 table"); break; }
     if ((e = cudaMemcpy(host_t, t, h * sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess) { status = cuda_fail(e, "copy"); break; }
     if ((e = cudaMemcpy(host_m, m, h * sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess) { status = cuda_fail(e, "copy"); break; }
@@ -691,14 +710,14 @@ fft_status fft_batch_create(fft_batch **batch, const fft_batch_item *items, int6
   b->ntiles = (int)h_tiles.size();
   do {
     if (count > 0) {
-      if ((e = cudaMalloc(&b->d_items, sizeof(BatchItem) * (size_t)count)) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc items"); break; }
+      if ((e = device_alloc(&b->d_items, sizeof(BatchItem) * (size_t)count)) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc items"); break; }
       if ((e = cudaMemcpy(b->d_items, h_items.data(), sizeof(BatchItem) * (size_t)count, cudaMemcpyHostToDevice)) != cudaSuccess) { status = cuda_fail(e, "copy items"); break; }
       b->device_bytes += (int64_t)(sizeof(BatchItem) * (size_t)count);
     }
     if (b->ntiles > 0) {
-      if ((e = cudaMalloc(&b->d_tiles, sizeof(BatchTile) * h_tiles.size())) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc tiles"); break; }
+      if ((e = device_alloc(&b->d_tiles, sizeof(BatchTile) * h_tiles.size())) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc tiles"); break; }
       if ((e = cudaMemcpy(b->d_tiles, h_tiles.data(), sizeof(BatchTile) * h_tiles.size(), cudaMemcpyHostToDevice)) != cudaSuccess) { status = cuda_fail(e, "copy tiles"); break; }
-      if ((e = cudaMalloc(&b->d_counter, sizeof(unsigned))) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc counter"); break; }
+      if ((e = device_alloc(&b->d_counter, sizeof(unsigned))) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc counter"); break; }
       if ((e = prepare_batch_kernel(&b->grid)) != cudaSuccess) { status = cuda_fail(e, "batch kernel attributes"); break; }
       b->device_bytes += (int64_t)(sizeof(BatchTile) * h_tiles.size() + sizeof(unsigned));
     }

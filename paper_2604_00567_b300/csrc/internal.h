@@ -118,6 +118,16 @@ struct PlanView {
 bool plan_view(const ::fft_plan *p, PlanView *v);
 void set_last_error(const char *msg);
 
+// cudaMalloc for every buffer the library owns.  Fault injection for tests:
+// with the environment variable DSFFT_FAULT_ALLOC=k set, the k-th call after
+// the variable took its current value fails with cudaErrorMemoryAllocation
+// (nothing is allocated); unset, it is plain cudaMalloc.
+cudaError_t device_alloc(void **ptr, size_t bytes);
+template <class T>
+cudaError_t device_alloc(T **ptr, size_t bytes) {
+  return device_alloc(reinterpret_cast<void **>(ptr), bytes);
+}
+
 // Radix-4 fused kernel (N <= 2^14): per-pass radix-4 table and first-stage
 // twiddles (fused4.cuh); `inverse` selects the +i of the inverse butterflies.
 struct Stage0R4;

@@ -91,8 +91,8 @@ fft_status fft_pipeline_create(fft_pipeline **pipe, const fft_plan *plan, int64_
   for (int i = 0; i < depth && e == cudaSuccess; ++i) {
     if ((e = cudaStreamCreateWithFlags(&p->streams[i], cudaStreamNonBlocking)) != cudaSuccess) break;
     if ((e = cudaEventCreateWithFlags(&p->done[i], cudaEventDisableTiming)) != cudaSuccess) break;
-    if ((e = cudaMalloc(&p->din[i], p->chunk_bytes)) != cudaSuccess) break;
-    e = cudaMalloc(&p->dout[i], p->chunk_bytes);
+    if ((e = device_alloc(&p->din[i], p->chunk_bytes)) != cudaSuccess) break;
+    e = device_alloc(&p->dout[i], p->chunk_bytes);
   }
   if (e != cudaSuccess) {
     release(p);

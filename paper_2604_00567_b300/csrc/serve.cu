@@ -447,16 +447,16 @@ fft_status fft_server_create(fft_server **server, const fft_server_opts *opts_in
   fft_status st = FFT_OK;
   do {
     if ((e = prepare_batch_kernel(&s->grid)) != cudaSuccess) { st = cuda_fail(e, "batch kernel attributes"); break; }
-    if ((e = cudaMalloc(&s->arena_base, o.memory_budget)) != cudaSuccess) { st = cuda_fail(e, "arena"); break; }
+    if ((e = device_alloc(&s->arena_base, o.memory_budget)) != cudaSuccess) { st = cuda_fail(e, "arena"); break; }
     s->arena.init(o.memory_budget);
     s->slots.resize((size_t)o.max_ticks_in_flight);
     const size_t ni = (size_t)o.max_tick_transforms;
     for (Slot &sl : s->slots) {
       if ((e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking)) != cudaSuccess) break;
       if ((e = cudaEventCreateWithFlags(&sl.event, cudaEventDisableTiming)) != cudaSuccess) break;
-      if ((e = cudaMalloc(&sl.d_items, ni * sizeof(BatchItem))) != cudaSuccess) break;
-      if ((e = cudaMalloc(&sl.d_tiles, ni * sizeof(BatchTile))) != cudaSuccess) break;
-      if ((e = cudaMalloc(&sl.d_counter, sizeof(unsigned))) != cudaSuccess) break;
+      if ((e = device_alloc(&sl.d_items, ni * sizeof(BatchItem))) != cudaSuccess) break;
+      if ((e = device_alloc(&sl.d_tiles, ni * sizeof(BatchTile))) != cudaSuccess) break;
+      if ((e = device_alloc(&sl.d_counter, sizeof(unsigned))) != cudaSuccess) break;
       if ((e = cudaHostAlloc(&sl.h_items, ni * sizeof(BatchItem), cudaHostAllocDefault)) != cudaSuccess) break;
       if ((e = cudaHostAlloc(&sl.h_tiles, ni * sizeof(BatchTile), cudaHostAllocDefault)) != cudaSuccess) break;
     }
