@@ -368,6 +368,7 @@ fft_status fft_plan_opts_init(fft_precision prec, fft_plan_opts *opts) {
 
 fft_status fft_plan_create(fft_plan **plan, int64_t n, fft_precision prec, fft_factorization fac,
                            const fft_plan_opts *opts_in) {
+  TraceRange trace("dsfft plan_create");
   if (!plan) return FFT_ERR_INVALID_ARG;
   *plan = nullptr;
   if (prec != FFT_PREC_FP32 && prec != FFT_PREC_FP16 && prec != FFT_PREC_BF16) return FFT_ERR_INVALID_ARG;
@@ -529,6 +530,7 @@ fft_status fft_exec(const fft_plan *plan, const void *in, void *out, int64_t bat
     snprintf(g_last_error, sizeof g_last_error, "in-place transforms are not supported by the HBM-sweep path");
     return FFT_ERR_UNSUPPORTED;
   }
+  TraceRange trace("dsfft exec");
   DeviceGuard guard(plan->device);
   if (guard.err != cudaSuccess) return cuda_fail(guard.err, "select device");
   cudaError_t e;
@@ -732,6 +734,7 @@ fft_status fft_batch_create(fft_batch **batch, const fft_batch_item *items, int6
 }
 
 fft_status fft_batch_exec(fft_batch *batch, void *stream) {
+  TraceRange trace("dsfft batch_exec");
   if (!batch) return FFT_ERR_INVALID_ARG;
   DeviceGuard guard(batch->device);
   if (guard.err != cudaSuccess) return cuda_fail(guard.err, "select device");
@@ -741,6 +744,7 @@ fft_status fft_batch_exec(fft_batch *batch, void *stream) {
 }
 
 fft_status fft_batch_exec_graph(fft_batch *batch, void *stream) {
+  TraceRange trace("dsfft batch_exec_graph");
   if (!batch) return FFT_ERR_INVALID_ARG;
   DeviceGuard guard(batch->device);
   if (guard.err != cudaSuccess) return cuda_fail(guard.err, "select device");

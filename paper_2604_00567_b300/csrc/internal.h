@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 struct fft_plan;   // the C ABI's opaque plan (defined in api.cu)
@@ -113,6 +114,15 @@ struct PlanView {
   const uint4 *twp[2];
   const Stage0Twiddles *tw0[2];   // host copies of the first per-pass entries
   int radix;                      // 2 or 4
+};
+
+// Host-side trace range around a library call (NVTX: visible in Nsight
+// timelines and usable as an ncu --nvtx filter; no cost without a tool).
+struct TraceRange {
+  explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange &) = delete;
+  TraceRange &operator=(const TraceRange &) = delete;
 };
 
 bool plan_view(const ::fft_plan *p, PlanView *v);

@@ -89,6 +89,7 @@ extern "C" fft_status fft_exec_batch_noalloc(const fft_noalloc_item *items, int6
   if (count > kMaxItems)
     return fail(FFT_ERR_INVALID_SIZE, "fft_exec_batch_noalloc: more than FFT_NOALLOC_MAX_ITEMS (4096) items");
   if (count == 0) return FFT_OK;
+  TraceRange trace("dsfft exec_batch_noalloc");
   int device = -1;
   for (int64_t i = 0; i < count; ++i) {
     const fft_noalloc_item &it = items[i];

@@ -108,6 +108,7 @@ fft_status fft_pipeline_exec(fft_pipeline *p, const void *host_in, void *host_ou
   if (dir != FFT_FORWARD && dir != FFT_INVERSE) return FFT_ERR_INVALID_ARG;
   if (batch == 0) return FFT_OK;
   if (!host_in || !host_out) return FFT_ERR_INVALID_ARG;
+  TraceRange trace("dsfft pipeline_exec");
   DeviceScope scope(p->view.device);
   cudaStream_t user = (cudaStream_t)stream;
   cudaError_t e = cudaEventRecord(p->start, user);

@@ -231,6 +231,7 @@ bool small_request(const Request *r) { return r->view.kernel == 0; }
 // Queue one tick on slot `sl` (no lock held; the requests are owned by the
 // tick).  Returns the first CUDA error.
 cudaError_t launch_tick(fft_server *s, Slot &sl) {
+  TraceRange trace("dsfft server tick");
   // small transforms, grouped by (plan, direction), larger sizes first
   std::vector<Request *> small;
   for (Request *r : sl.reqs)
