@@ -102,8 +102,10 @@ typedef struct fft_plan_opts {
     int32_t scale_inverse;  /* fft_scaling of inverse transforms */
     int32_t device;         /* CUDA device ordinal; -1 = current device */
     /* 1: when `variant` is AUTO, time every candidate variant for this
-     * (precision, N) on the plan's GPU at creation (about 128 MiB of scratch
-     * buffers, freed before returning) and keep the fastest; the choice is
+     * (precision, N) — for the sweeps also the split of the passes between
+     * the two sweeps, within one pass of the balanced split — on the plan's
+     * GPU at creation (about 128 MiB of scratch buffers, freed before
+     * returning) and keep the fastest; the choice is
      * cached per GPU model in the JSON file named by the environment variable
      * DSFFT_AUTOTUNE_CACHE, if set, and reused by later plans. 0: built-in
      * choice. */
@@ -121,7 +123,13 @@ typedef struct fft_plan_opts {
      * log2 N is odd.  Scaled directions divide by 4 per radix-4 pass.  The
      * results differ from the radix-2 algorithm's in rounding only. */
     int32_t radix;
-    int32_t reserved[2];    /* must be zero */
+    /* N > 2^14, radix 2: passes in the first of the two HBM sweeps (the
+     * second runs the rest; both must hold 7..12 passes).  0 = the balanced
+     * split ceil(log2 N / 2), or the autotuner's choice with autotune = 1.
+     * Nonzero selects the sweeps variant (FFT_ERR_UNSUPPORTED with another
+     * variant, radix 4 or N <= 2^14; FFT_ERR_INVALID_ARG outside 7..12). */
+    int32_t sweep_passes;
+    int32_t reserved[1];    /* must be zero */
 } fft_plan_opts;
 
 typedef struct fft_plan_info {
@@ -145,7 +153,7 @@ typedef struct fft_plan_info {
     int32_t variant;            /* fft_variant the plan runs */
     int32_t autotuned;          /* 1 = chosen by timing, 2 = from the cache */
     int32_t radix;              /* 2 or 4 */
-    int32_t reserved;
+    int32_t sweep_passes;       /* passes in sweep 1 when the plan runs sweeps, else 0 */
 } fft_plan_info;
 
 typedef struct fft_plan fft_plan;

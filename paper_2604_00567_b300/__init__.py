@@ -49,7 +49,7 @@ class PlanOpts(ctypes.Structure):
     _fields_ = [("lf_eps", ctypes.c_double), ("scale_forward", ctypes.c_int32),
                 ("scale_inverse", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("autotune", ctypes.c_int32), ("variant", ctypes.c_int32),
-                ("radix", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("radix", ctypes.c_int32), ("sweep_passes", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -61,7 +61,7 @@ class PlanInfo(ctypes.Structure):
                 ("scale_forward", ctypes.c_int32), ("scale_inverse", ctypes.c_int32),
                 ("cos_count", ctypes.c_int32), ("sin_count", ctypes.c_int32),
                 ("variant", ctypes.c_int32), ("autotuned", ctypes.c_int32), ("radix", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("sweep_passes", ctypes.c_int32)]
 
 
 class BatchItemC(ctypes.Structure):
@@ -194,7 +194,7 @@ class Plan:
     def __init__(self, n: int, precision: str = "fp32", factorization: str = "dual_select",
                  lf_eps: float = 1e-7, scale_forward: bool | None = None,
                  scale_inverse: bool | None = None, device: int | None = None,
-                 variant: str = "auto", autotune: bool = False, radix: int = 2):
+                 variant: str = "auto", autotune: bool = False, radix: int = 2, sweep_passes: int = 0):
         L = lib()
         self.n = int(n)
         self.precision = precision
@@ -211,6 +211,7 @@ class Plan:
         opts.variant = VARIANTS[variant]
         opts.autotune = 1 if autotune else 0
         opts.radix = int(radix)
+        opts.sweep_passes = int(sweep_passes)
         self.radix = int(radix)
         self.scale_forward = bool(opts.scale_forward)
         self.scale_inverse = bool(opts.scale_inverse)

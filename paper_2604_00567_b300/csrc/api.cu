@@ -40,6 +40,7 @@ struct fft_plan {
   uint4 *table4[2];     // radix-4: packed table, k in [0, 3N/4)
   uint4 *twp4[2];       // radix-4: per-pass table (N - 1 - log2 N mod 2 entries)
   Stage0R4 s0r4[2];     // radix-4: first-stage twiddles (host copy)
+  int sweep_ls1;        // sweeps: passes in sweep 1 (0: ceil(m/2))
 };
 
 namespace {
@@ -94,6 +95,19 @@ int default_variant(int prec, int log2n) {
   return FFT_VARIANT_SWEEPS;
 }
 
+// Built-in passes in sweep 1 for the sweeps variant (0: ceil(m/2)): the
+// split the autotuner measured fastest on a B300 (FP32 2^18: 8 + 10 passes
+// 26.2 % of HBM against 22.8 % for 9 + 9).
+int default_sweep_ls1(int prec, int log2n) {
+  switch (log2n) {
+    case 17: return 8;
+    case 18: return prec == kFP32 ? 8 : 9;
+    case 20: return prec == kFP32 ? 10 : 9;
+    case 22: return prec == kFP32 ? 11 : 12;
+  }
+  return 0;
+}
+
 // Make the plan run variant v (valid for its size): kernel choice and the
 // kernels' attributes on the current device.
 cudaError_t apply_variant(fft_plan *p, int v) {
@@ -103,7 +117,7 @@ cudaError_t apply_variant(fft_plan *p, int v) {
   p->shape = fused_shape(p->prec, p->log2n < kFusedMaxLog2N ? p->log2n : kFusedMaxLog2N, p->narrow);
   if (p->kernel == 0) return prepare_fused(p->prec, p->log2n, p->narrow);
   if (p->kernel == 2) return prepare_cluster(p->prec, p->log2n);
-  return prepare_sweeps(p->prec, p->log2n);
+  return prepare_sweeps(p->prec, p->log2n, p->sweep_ls1);
 }
 
 // Queue one transform batch of plan p on `stream` (d: 0 forward, 1 inverse).
@@ -118,7 +132,7 @@ cudaError_t plan_launch(const fft_plan *p, const void *in, void *out, int64_t ba
     return launch_fused(p->prec, p->log2n, p->narrow, scaled, in, out, batch, p->twp[d], p->tw0[d], stream);
   if (p->kernel == 2)
     return launch_cluster(p->prec, p->log2n, scaled, in, out, nullptr, batch, p->twp[d], p->tw0[d], stream);
-  return launch_sweeps(p->prec, p->log2n, scaled, in, out, nullptr, batch, p->twp[d], stream);
+  return launch_sweeps(p->prec, p->log2n, scaled, in, out, nullptr, batch, p->twp[d], stream, p->sweep_ls1);
 }
 
 // ---- autotune cache: a JSON object {"<gpu>|<prec>|<log2n>|<fac>": variant, ...}
@@ -162,10 +176,31 @@ void cache_write(const char *path, const std::map<std::string, int> &m) {
 
 // Time every valid variant of plan p on a 128 MiB batch and keep the
 // fastest (forward direction).
+// Candidate (variant, passes in sweep 1) of the autotuner: every variant
+// the size has, the sweeps with each valid split within one pass of the
+// balanced one.  Cached as variant * 100 + passes (0: the default split).
+struct Candidate {
+  int variant, ls1;
+};
+
+cudaError_t apply_candidate(fft_plan *p, const Candidate &c) {
+  p->sweep_ls1 = c.variant == FFT_VARIANT_SWEEPS ? c.ls1 : 0;
+  return apply_variant(p, c.variant);
+}
+
 cudaError_t autotune_plan(fft_plan *p) {
-  int cands[4], nc = 0;
-  for (int v = FFT_VARIANT_FUSED_WIDE; v <= FFT_VARIANT_SWEEPS; ++v)
-    if (variant_valid(p->prec, p->log2n, v)) cands[nc++] = v;
+  Candidate cands[8];
+  int nc = 0;
+  for (int v = FFT_VARIANT_FUSED_WIDE; v <= FFT_VARIANT_SWEEPS; ++v) {
+    if (!variant_valid(p->prec, p->log2n, v)) continue;
+    if (v != FFT_VARIANT_SWEEPS) {
+      cands[nc++] = Candidate{v, 0};
+      continue;
+    }
+    const int mid = (p->log2n + 1) / 2;
+    for (int l = mid - 1; l <= mid + 1; ++l)
+      if (sweep_ls1_valid(p->log2n, l)) cands[nc++] = Candidate{v, l == mid ? 0 : l};
+  }
   if (nc < 2) return cudaSuccess;
   cudaDeviceProp prop;
   cudaError_t e = cudaGetDeviceProperties(&prop, p->device);
@@ -177,9 +212,14 @@ cudaError_t autotune_plan(fft_plan *p) {
     std::lock_guard<std::mutex> lock(g_cache_mu);
     auto m = cache_read(path);
     auto it = m.find(key);
-    if (it != m.end() && variant_valid(p->prec, p->log2n, it->second)) {
-      p->autotuned = 2;
-      return apply_variant(p, it->second);
+    if (it != m.end()) {
+      const int val = it->second;
+      const Candidate c{val >= 100 ? val / 100 : val, val >= 100 ? val % 100 : 0};
+      if (variant_valid(p->prec, p->log2n, c.variant) &&
+          (c.ls1 == 0 || (c.variant == FFT_VARIANT_SWEEPS && sweep_ls1_valid(p->log2n, c.ls1)))) {
+        p->autotuned = 2;
+        return apply_candidate(p, c);
+      }
     }
   }
   const size_t eb = p->prec == kFP32 ? 8 : 4;
@@ -198,7 +238,7 @@ cudaError_t autotune_plan(fft_plan *p) {
     if ((e = cudaEventCreate(&a)) != cudaSuccess) break;
     if ((e = cudaEventCreate(&b)) != cudaSuccess) break;
     for (int c = 0; c < nc && e == cudaSuccess; ++c) {
-      if ((e = apply_variant(p, cands[c])) != cudaSuccess) break;
+      if ((e = apply_candidate(p, cands[c])) != cudaSuccess) break;
       for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = plan_launch(p, in, out, batch, 0, st);
       if (e != cudaSuccess) break;
       if ((e = cudaEventRecord(a, st)) != cudaSuccess) break;
@@ -209,7 +249,7 @@ cudaError_t autotune_plan(fft_plan *p) {
       float ms = 0.f;
       if ((e = cudaEventElapsedTime(&ms, a, b)) != cudaSuccess) break;
       if (best < 0 || ms < best_ms) {
-        best = cands[c];
+        best = c;
         best_ms = ms;
       }
     }
@@ -224,10 +264,10 @@ cudaError_t autotune_plan(fft_plan *p) {
   if (path && *path) {
     std::lock_guard<std::mutex> lock(g_cache_mu);
     auto m = cache_read(path);
-    m[key] = best;
+    m[key] = cands[best].ls1 ? cands[best].variant * 100 + cands[best].ls1 : cands[best].variant;
     cache_write(path, m);
   }
-  return apply_variant(p, best);
+  return apply_candidate(p, cands[best]);
 }
 
 int ilog2_exact(int64_t n) {
@@ -254,6 +294,7 @@ bool dsfft::plan_view(const fft_plan *p, PlanView *v) {
   v->tw0[0] = &p->tw0[0];
   v->tw0[1] = &p->tw0[1];
   v->radix = p->radix;
+  v->sweep_ls1 = p->sweep_ls1;
   return true;
 }
 
@@ -318,7 +359,7 @@ cudaError_t batch_enqueue(const fft_batch *b, cudaStream_t stream) {
                          p->tw0[g.dir], stream);
     else
       e = launch_sweeps(p->prec, p->log2n, scaled, nullptr, nullptr, b->d_items + g.first, g.count, p->twp[g.dir],
-                        stream);
+                        stream, p->sweep_ls1);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -383,6 +424,7 @@ fft_status fft_plan_create(fft_plan **plan, int64_t n, fft_precision prec, fft_f
   }
   if (opts.autotune != 0 && opts.autotune != 1) return FFT_ERR_INVALID_ARG;
   if (opts.radix != 0 && opts.radix != 2 && opts.radix != 4) return FFT_ERR_INVALID_ARG;
+  if (opts.sweep_passes != 0 && (opts.sweep_passes < 7 || opts.sweep_passes > 12)) return FFT_ERR_INVALID_ARG;
   if (opts.variant < FFT_VARIANT_AUTO || opts.variant > FFT_VARIANT_SWEEPS) return FFT_ERR_INVALID_ARG;
   if (!(opts.lf_eps > 0.0) || !(opts.lf_eps < 1.0)) return FFT_ERR_INVALID_ARG;
   for (int s : {opts.scale_forward, opts.scale_inverse})
@@ -394,6 +436,12 @@ fft_status fft_plan_create(fft_plan **plan, int64_t n, fft_precision prec, fft_f
   if (radix == 4 && opts.variant != FFT_VARIANT_AUTO && opts.variant != r4_variant) {
     snprintf(g_last_error, sizeof g_last_error, "radix-4 plans run the fused radix-4 kernel (N <= 2^%d) or "
              "radix-4 sweeps", kFusedMaxLog2N);
+    return FFT_ERR_UNSUPPORTED;
+  }
+  if (opts.sweep_passes != 0 &&
+      (radix == 4 || (opts.variant != FFT_VARIANT_AUTO && opts.variant != FFT_VARIANT_SWEEPS) ||
+       !sweep_ls1_valid(log2n, opts.sweep_passes) || log2n <= kFusedMaxLog2N)) {
+    snprintf(g_last_error, sizeof g_last_error, "sweep_passes %d does not exist for this plan", opts.sweep_passes);
     return FFT_ERR_UNSUPPORTED;
   }
   if (opts.variant != FFT_VARIANT_AUTO && !variant_valid(prec, log2n, opts.variant)) {
@@ -480,9 +528,11 @@ fft_status fft_plan_create(fft_plan **plan, int64_t n, fft_precision prec, fft_f
       if (e != cudaSuccess) { status = cuda_fail(e, "kernel attributes"); break; }
       break;
     }
-    const int v = opts.variant != FFT_VARIANT_AUTO ? opts.variant : default_variant(prec, log2n);
+    p->sweep_ls1 = opts.sweep_passes ? opts.sweep_passes : default_sweep_ls1(prec, log2n);
+    const int v = opts.sweep_passes ? FFT_VARIANT_SWEEPS
+                  : opts.variant != FFT_VARIANT_AUTO ? opts.variant : default_variant(prec, log2n);
     if ((e = apply_variant(p, v)) != cudaSuccess) { status = cuda_fail(e, "kernel attributes"); break; }
-    if (opts.autotune && opts.variant == FFT_VARIANT_AUTO && (e = autotune_plan(p)) != cudaSuccess) { status = cuda_fail(e, "autotune"); break; }
+    if (opts.autotune && opts.variant == FFT_VARIANT_AUTO && !opts.sweep_passes && (e = autotune_plan(p)) != cudaSuccess) { status = cuda_fail(e, "autotune"); break; }
   } while (0);
   if (st) cudaStreamDestroy(st);
   if (counts) cudaFree(counts);
@@ -589,6 +639,13 @@ fft_status fft_plan_get_info(const fft_plan *plan, fft_plan_info *info) {
   info->variant = plan->variant;
   info->autotuned = plan->autotuned;
   info->radix = plan->radix;
+  info->sweep_passes = 0;
+  if (plan->kernel == 1) {
+    int l1, l2;
+    if (plan->radix == 4) sweep_split4(plan->log2n, &l1, &l2);
+    else sweep_split(plan->log2n, &l1, &l2);
+    info->sweep_passes = plan->sweep_ls1 ? plan->sweep_ls1 : l1;
+  }
   return FFT_OK;
 }
 

@@ -80,13 +80,15 @@ struct Stage0Twiddles {
 cudaError_t launch_fused(int prec, int log2n, bool narrow, bool scaled, const void *in, void *out, int64_t batch,
                          const uint4 *twp, const Stage0Twiddles &tw0, cudaStream_t stream);
 
-// N > 2^14: two sweeps over HBM (passes [0, ceil(m/2)) then the rest).
+// N > 2^14: two sweeps over HBM (passes [0, ls1) then the rest; ls1 = 0
+// picks ceil(m/2)).  Both sweeps hold 7..12 passes (sweep_ls1_valid).
 // `in` and `out` must differ; sweep 2 runs in place on `out`.
 void sweep_split(int log2n, int *ls1, int *ls2);
-cudaError_t prepare_sweeps(int prec, int log2n);
+bool sweep_ls1_valid(int log2n, int ls1);
+cudaError_t prepare_sweeps(int prec, int log2n, int ls1 = 0);
 // `items` (device array, one per transform) replaces in/out when non-null.
 cudaError_t launch_sweeps(int prec, int log2n, bool scaled, const void *in, void *out, const BatchItem *items,
-                          int64_t batch, const uint4 *twp, cudaStream_t stream);
+                          int64_t batch, const uint4 *twp, cudaStream_t stream, int ls1 = 0);
 
 // Radix-4 plans, N > 2^14: two sweeps of whole radix-4 passes (sweep 1 also
 // holds the radix-2 pass of an odd log2 N); `twp4` the per-pass radix-4
@@ -114,6 +116,7 @@ struct PlanView {
   const uint4 *twp[2];
   const Stage0Twiddles *tw0[2];   // host copies of the first per-pass entries
   int radix;                      // 2 or 4
+  int sweep_ls1;                  // passes in sweep 1 (0: ceil(m/2))
 };
 
 // Host-side trace range around a library call (NVTX: visible in Nsight

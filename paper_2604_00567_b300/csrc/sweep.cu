@@ -326,11 +326,17 @@ void sweep_split4(int log2n, int *ls1, int *ls2) {
   *ls2 = 2 * (n4 - a);
 }
 
+bool sweep_ls1_valid(int log2n, int ls1) { return ls1 >= 7 && ls1 <= 12 && log2n - ls1 >= 7 && log2n - ls1 <= 12; }
+
 template <bool R4>
-static cudaError_t prepare_sweeps_impl(int prec, int log2n) {
+static cudaError_t prepare_sweeps_impl(int prec, int log2n, int ls1_req = 0) {
   int ls1, ls2;
   if (R4) sweep_split4(log2n, &ls1, &ls2);
   else sweep_split(log2n, &ls1, &ls2);
+  if (!R4 && ls1_req > 0) {
+    ls1 = ls1_req;
+    ls2 = log2n - ls1_req;
+  }
   if (ls1 < 7 || ls1 > 12 || ls2 < 7 || ls2 > 12) return cudaErrorInvalidValue;
   for (int ls : {ls1, ls2}) {
     cudaError_t e = prec == kFP32 ? SweepSet<kFP32, R4>::prepare(ls)
@@ -343,10 +349,14 @@ static cudaError_t prepare_sweeps_impl(int prec, int log2n) {
 template <bool R4>
 static cudaError_t launch_sweeps_impl(int prec, int log2n, bool scaled, const void *in, void *out,
                                       const BatchItem *items, int64_t batch, const uint4 *twp, const uint4 &r2e,
-                                      uint32_t sgn, cudaStream_t stream) {
+                                      uint32_t sgn, cudaStream_t stream, int ls1_req = 0) {
   int ls1, ls2;
   if (R4) sweep_split4(log2n, &ls1, &ls2);
   else sweep_split(log2n, &ls1, &ls2);
+  if (!R4 && ls1_req > 0) {
+    ls1 = ls1_req;
+    ls2 = log2n - ls1_req;
+  }
   if (ls1 < 7 || ls1 > 12 || ls2 < 7 || ls2 > 12) return cudaErrorInvalidValue;
   auto get = [&](bool last, int ls) {
     return prec == kFP32 ? SweepSet<kFP32, R4>::get(scaled, last, ls)
@@ -357,11 +367,11 @@ static cudaError_t launch_sweeps_impl(int prec, int log2n, bool scaled, const vo
   return get(true, ls2)(out, out, items, batch, log2n, ls1, twp, r2e, sgn, stream);
 }
 
-cudaError_t prepare_sweeps(int prec, int log2n) { return prepare_sweeps_impl<false>(prec, log2n); }
+cudaError_t prepare_sweeps(int prec, int log2n, int ls1) { return prepare_sweeps_impl<false>(prec, log2n, ls1); }
 
 cudaError_t launch_sweeps(int prec, int log2n, bool scaled, const void *in, void *out, const BatchItem *items,
-                          int64_t batch, const uint4 *twp, cudaStream_t stream) {
-  return launch_sweeps_impl<false>(prec, log2n, scaled, in, out, items, batch, twp, uint4{}, 0u, stream);
+                          int64_t batch, const uint4 *twp, cudaStream_t stream, int ls1) {
+  return launch_sweeps_impl<false>(prec, log2n, scaled, in, out, items, batch, twp, uint4{}, 0u, stream, ls1);
 }
 
 cudaError_t prepare_sweeps4(int prec, int log2n) { return prepare_sweeps_impl<true>(prec, log2n); }

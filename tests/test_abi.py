@@ -53,7 +53,7 @@ def test_opts_defaults(lib):
     o = dsfft.PlanOpts()
     assert lib.fft_plan_opts_init(1, ctypes.byref(o)) == 0
     assert o.lf_eps == 1e-7 and o.scale_forward == 1 and o.scale_inverse == 0 and o.device == -1
-    assert o.autotune == 0 and o.variant == 0 and o.radix == 0
+    assert o.autotune == 0 and o.variant == 0 and o.radix == 0 and o.sweep_passes == 0
     assert lib.fft_plan_opts_init(0, ctypes.byref(o)) == 0
     assert o.scale_forward == 0
     assert lib.fft_plan_opts_init(7, ctypes.byref(o)) == 1
@@ -75,8 +75,16 @@ def test_host_side_validation_without_gpu(lib):
     o.lf_eps = 0.0
     assert lib.fft_plan_create(ctypes.byref(h), 1024, 0, 0, ctypes.byref(o)) == 1
     lib.fft_plan_opts_init(0, ctypes.byref(o))
-    o.reserved[1] = 5
+    o.reserved[0] = 5
     assert lib.fft_plan_create(ctypes.byref(h), 1024, 0, 2, ctypes.byref(o)) == 1
+    lib.fft_plan_opts_init(0, ctypes.byref(o))
+    o.sweep_passes = 6
+    assert lib.fft_plan_create(ctypes.byref(h), 1 << 18, 0, 2, ctypes.byref(o)) == 1   # outside 7..12
+    o.sweep_passes = 9
+    assert lib.fft_plan_create(ctypes.byref(h), 1024, 0, 2, ctypes.byref(o)) == 3      # no sweeps at 2^10
+    assert lib.fft_plan_create(ctypes.byref(h), 1 << 22, 0, 2, ctypes.byref(o)) == 3   # 9 + 13 passes
+    o.variant = 3
+    assert lib.fft_plan_create(ctypes.byref(h), 1 << 16, 0, 2, ctypes.byref(o)) == 3   # cluster has no sweeps
     lib.fft_plan_opts_init(0, ctypes.byref(o))
     o.radix = 3
     assert lib.fft_plan_create(ctypes.byref(h), 1024, 0, 2, ctypes.byref(o)) == 1

@@ -64,3 +64,40 @@ def test_autotune_and_cache(dsfft, tmp_path, monkeypatch):
     # a single-candidate size needs no tuning
     p4 = dsfft.Plan(16, "fp16", "dual_select", autotune=True)
     assert p4.info()["autotuned"] == 0
+
+
+@pytest.mark.parametrize("prec,log2n,splits", [("fp16", 18, (8, 9, 10)), ("fp32", 17, (8, 9, 10)),
+                                               ("bf16", 20, (9, 10, 11))])
+def test_sweep_splits_agree(dsfft, prec, log2n, splits):
+    """Any split of the passes between the two sweeps runs the same
+    butterflies: identical bytes; the plan reports the split it runs."""
+    import torch
+    N = 1 << log2n
+    x = signals.device_signal(2, N, prec, seed=log2n)
+    outs = []
+    for sp in splits:
+        plan = dsfft.Plan(N, prec, "dual_select", sweep_passes=sp)
+        info = plan.info()
+        assert info["variant_name"] == "sweeps" and info["sweep_passes"] == sp
+        outs.append(plan.exec(x))
+    torch.cuda.synchronize()
+    word = torch.int32 if prec == "fp32" else torch.int16
+    for y in outs[1:]:
+        assert torch.equal(y.view(word), outs[0].view(word))
+
+
+def test_autotune_sweep_split_cached(dsfft, tmp_path, monkeypatch):
+    """The autotuner also times the sweep splits; a cached split is reused."""
+    import json
+    cache = tmp_path / "tune.json"
+    monkeypatch.setenv("DSFFT_AUTOTUNE_CACHE", str(cache))
+    p1 = dsfft.Plan(1 << 18, "fp16", "dual_select", autotune=True)
+    i1 = p1.info()
+    assert i1["autotuned"] == 1 and i1["variant_name"] == "sweeps" and 8 <= i1["sweep_passes"] <= 10
+    data = json.loads(cache.read_text())
+    key = [k for k in data if k.endswith("|1|18|2")][0]
+    data[key] = 4 * 100 + 10          # sweeps with 10 passes in sweep 1
+    cache.write_text(json.dumps(data))
+    p2 = dsfft.Plan(1 << 18, "fp16", "dual_select", autotune=True)
+    i2 = p2.info()
+    assert i2["autotuned"] == 2 and i2["sweep_passes"] == 10
