@@ -664,7 +664,7 @@ def main():
                     choices=["dual_select", "linzer_feig_clamped", "cosine"])
     ap.add_argument("--batch-mib", type=int, default=256)
     ap.add_argument("--variant", default="auto",
-                    choices=["auto", "fused_wide", "fused_narrow", "cluster", "sweeps"])
+                    choices=["auto", "fused_wide", "fused_narrow", "cluster", "sweeps", "fused_tma"])
     ap.add_argument("--iters", type=int, default=2)
     args = ap.parse_args()
     if args.exec_only is not None:

@@ -93,7 +93,12 @@ typedef enum fft_variant {
                                       that keeps a transform within 1024 threads) */
     FFT_VARIANT_CLUSTER = 3,       /* 2^15 <= N <= 2^17 (FP16/BF16), <= 2^16 (FP32):
                                       one launch on a thread-block cluster */
-    FFT_VARIANT_SWEEPS = 4         /* N >= 2^15: two HBM sweeps */
+    FFT_VARIANT_SWEEPS = 4,        /* N >= 2^15: two HBM sweeps */
+    FFT_VARIANT_FUSED_TMA = 5      /* 2^8 <= N <= 2^14 (FP32: 2^13): the wide fused kernel as a
+                                      persistent grid whose input tiles arrive by
+                                      double-buffered bulk asynchronous copies
+                                      (TMA); inputs not 16-byte aligned run the
+                                      wide kernel */
 } fft_variant;
 
 typedef struct fft_plan_opts {
@@ -204,6 +209,14 @@ DSFFT_API fft_status fft_plan_get_table(const fft_plan *plan, fft_direction dir,
  * on a scaled direction; same entry layout as fft_plan_get_table) to host
  * memory.  FFT_ERR_UNSUPPORTED for a radix-2 plan. */
 DSFFT_API fft_status fft_plan_get_table4(const fft_plan *plan, fft_direction dir, void *host_dst, size_t bytes);
+
+/* Read and clear the plan's device error word.  Kernels whose waits are
+ * bounded (the FFT_VARIANT_FUSED_TMA kernel waits at most about one second
+ * for each bulk copy) set it when such a wait gives up; the affected blocks
+ * then skip their remaining transforms, so the output is incomplete.
+ * Returns FFT_ERR_TIMEOUT if it was set since the last call, else FFT_OK.
+ * Synchronous: waits for all work queued on the plan's device first. */
+DSFFT_API fft_status fft_plan_device_status(const fft_plan *plan);
 
 /* Describe the plan (kernel choice, launch shape, table sizes). */
 DSFFT_API fft_status fft_plan_get_info(const fft_plan *plan, fft_plan_info *info);

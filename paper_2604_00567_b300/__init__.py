@@ -41,7 +41,7 @@ class DsfftError(RuntimeError):
         super().__init__(f"{where}: {STATUS.get(status, status)}" + (f" ({detail})" if detail else ""))
 
 
-VARIANTS = {"auto": 0, "fused_wide": 1, "fused_narrow": 2, "cluster": 3, "sweeps": 4}
+VARIANTS = {"auto": 0, "fused_wide": 1, "fused_narrow": 2, "cluster": 3, "sweeps": 4, "fused_tma": 5}
 VARIANT_NAMES = {v: k for k, v in VARIANTS.items()}
 
 
@@ -134,6 +134,7 @@ def lib():
             L.fft_plan_get_table.argtypes = [P, i32, P, ctypes.c_size_t]
             L.fft_plan_get_table4.argtypes = [P, i32, P, ctypes.c_size_t]
             L.fft_plan_get_info.argtypes = [P, ctypes.POINTER(PlanInfo)]
+            L.fft_plan_device_status.argtypes = [P]
             L.fft_twiddle_fp64.argtypes = [i64, i32, d, P, P, P]
             L.fft_status_string.restype = ctypes.c_char_p
             L.fft_status_string.argtypes = [i32]
@@ -164,7 +165,8 @@ def lib():
             L.fft_server_get_stats.argtypes = [P, ctypes.POINTER(ServerStatsC)]
             L.fft_server_destroy.argtypes = [P]
             for name in ("fft_plan_opts_init", "fft_plan_create", "fft_plan_destroy", "fft_exec",
-                         "fft_plan_get_table", "fft_plan_get_table4", "fft_plan_get_info", "fft_twiddle_fp64", "fft_batch_create",
+                         "fft_plan_get_table", "fft_plan_get_table4", "fft_plan_get_info", "fft_plan_device_status",
+                         "fft_twiddle_fp64", "fft_batch_create",
                          "fft_batch_exec", "fft_batch_exec_graph", "fft_batch_get_info", "fft_batch_destroy",
                          "fft_exec_batch_noalloc", "fft_pipeline_create", "fft_pipeline_exec",
                          "fft_pipeline_destroy", "fft_server_opts_init", "fft_server_create",
@@ -249,6 +251,11 @@ class Plan:
         d = {k: getattr(inf, k) for k, _ in PlanInfo._fields_}
         d["variant_name"] = VARIANT_NAMES.get(d["variant"], "?")
         return d
+
+    def device_status(self) -> None:
+        """Raise DsfftError (FFT_ERR_TIMEOUT) if a bounded device-side wait
+        of this plan's kernels gave up since the last call; clears the word."""
+        _check(lib().fft_plan_device_status(self._h), "fft_plan_device_status")
 
     def element_bytes(self) -> int:
         return 8 if self.precision == "fp32" else 4

@@ -41,6 +41,9 @@ struct fft_plan {
   uint4 *twp4[2];       // radix-4: per-pass table (N - 1 - log2 N mod 2 entries)
   Stage0R4 s0r4[2];     // radix-4: first-stage twiddles (host copy)
   int sweep_ls1;        // sweeps: passes in sweep 1 (0: ceil(m/2))
+  int tma_grid;         // fused_tma: resident blocks of the device
+  uint32_t tma_tx_extra;  // fused_tma: fault injection (DSFFT_FAULT_TMA_WAIT), else 0
+  int *status;          // device error word of the bounded waits
 };
 
 namespace {
@@ -79,6 +82,7 @@ bool variant_valid(int prec, int log2n, int v) {
     case FFT_VARIANT_FUSED_NARROW: return log2n <= kFusedMaxLog2N && fused_has_narrow(prec, log2n);
     case FFT_VARIANT_CLUSTER: return log2n > kFusedMaxLog2N && cluster_log2k(prec, log2n) >= 0;
     case FFT_VARIANT_SWEEPS: return log2n > kFusedMaxLog2N;
+    case FFT_VARIANT_FUSED_TMA: return fused_tma_valid(prec, log2n);
   }
   return false;
 }
@@ -113,8 +117,16 @@ int default_sweep_ls1(int prec, int log2n) {
 cudaError_t apply_variant(fft_plan *p, int v) {
   p->variant = v;
   p->narrow = v == FFT_VARIANT_FUSED_NARROW;
-  p->kernel = v == FFT_VARIANT_FUSED_WIDE || v == FFT_VARIANT_FUSED_NARROW ? 0 : v == FFT_VARIANT_CLUSTER ? 2 : 1;
+  p->kernel = v == FFT_VARIANT_FUSED_WIDE || v == FFT_VARIANT_FUSED_NARROW || v == FFT_VARIANT_FUSED_TMA ? 0
+              : v == FFT_VARIANT_CLUSTER                                                                  ? 2
+                                                                                                          : 1;
   p->shape = fused_shape(p->prec, p->log2n < kFusedMaxLog2N ? p->log2n : kFusedMaxLog2N, p->narrow);
+  if (v == FFT_VARIANT_FUSED_TMA) {
+    p->shape = fused_tma_shape(p->prec, p->log2n);
+    // the wide kernel also runs, for inputs that are not 16-byte aligned
+    const cudaError_t e = prepare_fused(p->prec, p->log2n, false);
+    return e != cudaSuccess ? e : prepare_fused_tma(p->prec, p->log2n, &p->tma_grid);
+  }
   if (p->kernel == 0) return prepare_fused(p->prec, p->log2n, p->narrow);
   if (p->kernel == 2) return prepare_cluster(p->prec, p->log2n);
   return prepare_sweeps(p->prec, p->log2n, p->sweep_ls1);
@@ -128,6 +140,9 @@ cudaError_t plan_launch(const fft_plan *p, const void *in, void *out, int64_t ba
       return launch_sweeps4(p->prec, p->log2n, scaled, d, in, out, nullptr, batch, p->twp4[d], p->s0r4[d].r2, stream);
     return launch_fused4(p->prec, p->log2n, scaled, d, in, out, batch, p->twp4[d], p->s0r4[d], stream);
   }
+  if (p->variant == FFT_VARIANT_FUSED_TMA && ((uintptr_t)in & 15) == 0)
+    return launch_fused_tma(p->prec, p->log2n, scaled, in, out, batch, p->twp[d], p->tw0[d], p->tma_grid, p->status,
+                            p->tma_tx_extra, stream);
   if (p->kernel == 0)
     return launch_fused(p->prec, p->log2n, p->narrow, scaled, in, out, batch, p->twp[d], p->tw0[d], stream);
   if (p->kernel == 2)
@@ -191,7 +206,7 @@ cudaError_t apply_candidate(fft_plan *p, const Candidate &c) {
 cudaError_t autotune_plan(fft_plan *p) {
   Candidate cands[8];
   int nc = 0;
-  for (int v = FFT_VARIANT_FUSED_WIDE; v <= FFT_VARIANT_SWEEPS; ++v) {
+  for (int v = FFT_VARIANT_FUSED_WIDE; v <= FFT_VARIANT_FUSED_TMA; ++v) {
     if (!variant_valid(p->prec, p->log2n, v)) continue;
     if (v != FFT_VARIANT_SWEEPS) {
       cands[nc++] = Candidate{v, 0};
@@ -425,7 +440,7 @@ fft_status fft_plan_create(fft_plan **plan, int64_t n, fft_precision prec, fft_f
   if (opts.autotune != 0 && opts.autotune != 1) return FFT_ERR_INVALID_ARG;
   if (opts.radix != 0 && opts.radix != 2 && opts.radix != 4) return FFT_ERR_INVALID_ARG;
   if (opts.sweep_passes != 0 && (opts.sweep_passes < 7 || opts.sweep_passes > 12)) return FFT_ERR_INVALID_ARG;
-  if (opts.variant < FFT_VARIANT_AUTO || opts.variant > FFT_VARIANT_SWEEPS) return FFT_ERR_INVALID_ARG;
+  if (opts.variant < FFT_VARIANT_AUTO || opts.variant > FFT_VARIANT_FUSED_TMA) return FFT_ERR_INVALID_ARG;
   if (!(opts.lf_eps > 0.0) || !(opts.lf_eps < 1.0)) return FFT_ERR_INVALID_ARG;
   for (int s : {opts.scale_forward, opts.scale_inverse})
     if (s != FFT_SCALE_NONE && s != FFT_SCALE_HALF_PER_PASS) return FFT_ERR_INVALID_ARG;
@@ -465,6 +480,7 @@ fft_status fft_plan_create(fft_plan **plan, int64_t n, fft_precision prec, fft_f
   p->scale[1] = opts.scale_inverse;
   p->device = device;
   p->radix = radix;
+  if (const char *f = getenv("DSFFT_FAULT_TMA_WAIT")) p->tma_tx_extra = atoi(f) > 0 ? 16u : 0u;
 
   const size_t entries = (size_t)(n / 2);
   // per-pass tables hold the compact 8-byte entries for FP16/BF16
@@ -482,8 +498,10 @@ fft_status fft_plan_create(fft_plan **plan, int64_t n, fft_precision prec, fft_f
     if ((e = device_alloc(&p->twp[1], (size_t)(n - 1) * tw_bytes)) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc table"); break; }
     if ((e = device_alloc(&counts, 2 * sizeof(int))) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc counts"); break; }
     if ((e = device_alloc(&head, 4 * 31 * sizeof(uint4))) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc"); break; }
+    if ((e = device_alloc(&p->status, 16)) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc status"); break; }
     if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) { status = cuda_fail(e, "stream"); break; }
     if ((e = cudaMemsetAsync(counts, 0, 2 * sizeof(int), st)) != cudaSuccess) { status = cuda_fail(e, "memset"); break; }
+    if ((e = cudaMemsetAsync(p->status, 0, 16, st)) != cudaSuccess) { status = cuda_fail(e, "memset"); break; }
     if ((e = launch_build_table(log2n, n / 2, fac, opts.lf_eps, prec, 0, p->scale[0] ? 0.5 : 1.0, p->table[0], counts, st)) != cudaSuccess) { status = cuda_fail(e, "table build"); break; }
     if ((e = launch_build_table(log2n, n / 2, fac, opts.lf_eps, prec, 1, p->scale[1] ? 0.5 : 1.0, p->table[1], nullptr, st)) != cudaSuccess) { status = cuda_fail(e, "table build"); break; }
     const int64_t cnt0 = (n < 32 ? n : 32) - 1;
@@ -544,6 +562,7 @@ fft_status fft_plan_create(fft_plan **plan, int64_t n, fft_precision prec, fft_f
       if (p->table4[d]) cudaFree(p->table4[d]);
       if (p->twp4[d]) cudaFree(p->twp4[d]);
     }
+    if (p->status) cudaFree(p->status);
     delete p;
     return status;
   }
@@ -562,6 +581,7 @@ fft_status fft_plan_destroy(fft_plan *plan) {
     if (plan->table4[d]) cudaFree(plan->table4[d]);
     if (plan->twp4[d]) cudaFree(plan->twp4[d]);
   }
+  if (plan->status) cudaFree(plan->status);
   delete plan;
   return FFT_OK;
 }
@@ -588,6 +608,22 @@ fft_status fft_exec(const fft_plan *plan, const void *in, void *out, int64_t bat
   if (e != cudaSuccess) {
     static const char *what[3] = {"fused kernel launch", "sweep kernel launch", "cluster kernel launch"};
     return cuda_fail(e, what[plan->kernel]);
+  }
+  return FFT_OK;
+}
+
+fft_status fft_plan_device_status(const fft_plan *plan) {
+  if (!plan) return FFT_ERR_INVALID_ARG;
+  DeviceGuard guard(plan->device);
+  if (guard.err != cudaSuccess) return cuda_fail(guard.err, "select device");
+  int word = 0;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&word, plan->status, sizeof word, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && word != 0) e = cudaMemset(plan->status, 0, sizeof word);
+  if (e != cudaSuccess) return cuda_fail(e, "read device status");
+  if (word != 0) {
+    snprintf(g_last_error, sizeof g_last_error, "a bounded wait for bulk copies gave up (status word 0x%x)", word);
+    return FFT_ERR_TIMEOUT;
   }
   return FFT_OK;
 }

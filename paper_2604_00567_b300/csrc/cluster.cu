@@ -13,7 +13,10 @@
 //            q / GC1 (DSMEM loads), runs passes [LS1, m) and stores
 //            X[g' + o M1] to HBM.
 // A second cluster barrier separates the remote reads from the reuse of the
-// buffer for phase 2's own exchanges.  Every radix-2 butterfly of the
+// buffer for phase 2's own exchanges (and from the owner's exit); it is
+// split: each thread arrives once its remote reads are done and waits only
+// before its first write to the buffer, so the first register stage of
+// phase 2 runs while the other CTAs finish their reads.  Every radix-2 butterfly of the
 // pass-by-pass algorithm is executed with its own operands and twiddle, so
 // the output is bit-identical to it; HBM sees one read and one write.
 //
@@ -109,7 +112,7 @@ __global__ void __cluster_dims__(1 << LOG2K, 1, 1)
     E *grp = sm + lg * K::S1;
     K::P1::template run<true>(
         v, tid, 0, twp, tw0f, [&](int idx, E val) { grp[idx] = val; }, [&](int idx) { return grp[idx]; },
-        [] { __syncthreads(); }, [&](int o, E val) { grp[o] = val; });
+        [] { __syncthreads(); }, [&](int o, E val) { grp[o] = val; }, [] {});
   }
   cluster.sync();   // Z_LS1 complete in every CTA of the cluster
   // ---- phase 2: passes [LS1, m) ----
@@ -134,12 +137,15 @@ __global__ void __cluster_dims__(1 << LOG2K, 1, 1)
       constexpr int gl0 = (p * K::P2::T) % K::GC1;
       dsmem_ld(rbase[owner] + (uint32_t)(gl0 * K::S1 * (int)sizeof(E)), v[p]);
     });
-    cluster.sync();   // every remote read done before the buffer is reused
+    // arrive: this thread's remote reads are done (release orders them
+    // first); wait: every CTA's reads of this buffer are done
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
     E *grp = sm + lg * K::S2;
     E *dst = io.dst(tr) + gp;
     K::P2::template run<false>(
         v, tid, gp, twp, tw0f, [&](int idx, E val) { grp[idx] = val; }, [&](int idx) { return grp[idx]; },
-        [] { __syncthreads(); }, [&](int o, E val) { cl_stcs(dst + (int64_t)o * K::M1, val); });
+        [] { __syncthreads(); }, [&](int o, E val) { cl_stcs(dst + (int64_t)o * K::M1, val); },
+        [] { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); });
   }
 }
 

@@ -115,7 +115,9 @@ struct Fused {
     });
   }
 
-  template <int S, class TW0>
+  // SIN: the first stage's values were read from `sm` (the bulk-copied
+  // input), so its exchange must wait until every thread has read them.
+  template <int S, class TW0, bool SIN = false>
   static __device__ __forceinline__ void stages(E (&v)[R], E *sm, int tid, int lt, const uint4 *__restrict__ tw,
                                                 const TW0 &tw0, E *dst, bool active) {
     constexpr int P = S * LOG2R;
@@ -143,7 +145,7 @@ struct Fused {
         });
       }
     } else {
-      if constexpr (S > 0) sync(lt);   // previous exchange fully read
+      if constexpr (S > 0 || SIN) sync(lt);   // previous exchange (or the input) fully read
       // pad(base + off) = pad(base) + off + off / 32 when off is a multiple
       // of 32 (P >= 5) or base is and off < 32 (P = 0, RHO = 5)
       constexpr bool FOLD = P >= 5 || (P == 0 && RHO == 5);
@@ -160,7 +162,7 @@ struct Fused {
         });
       });
       sync(lt);
-      stages<S + 1>(v, sm, tid, lt, tw, tw0, dst, active);
+      stages<S + 1, TW0, SIN>(v, sm, tid, lt, tw, tw0, dst, active);
     }
   }
 

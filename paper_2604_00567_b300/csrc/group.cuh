@@ -68,10 +68,12 @@ struct GroupPasses {
   // Stockham index idx of this group in the exchange buffer, sync() orders
   // the block between them, out(o, value) receives local output o.  With
   // SYNC_OUT the block synchronises before the outputs (when out() writes
-  // the exchange buffer).
-  template <bool SYNC_OUT = false, int S = 0, class TW0, class XW, class XR, class SYNC, class OUT>
+  // the exchange buffer).  first_write() runs once, after the first register
+  // stage and before the first write to the exchange buffer or output.
+  template <bool SYNC_OUT = false, int S = 0, class TW0, class XW, class XR, class SYNC, class OUT, class FW>
   static __device__ __forceinline__ void run(E (&v)[R], int tid, int jg, const uint4 *__restrict__ twp,
-                                             const TW0 &tw0, XW &&xw, XR &&xr, SYNC &&sync, OUT &&out) {
+                                             const TW0 &tw0, XW &&xw, XR &&xr, SYNC &&sync, OUT &&out,
+                                             FW &&first_write) {
     constexpr int PL = S * LOG2R;
     constexpr int RHO = (LS - PL) < LOG2R ? (LS - PL) : LOG2R;
     constexpr int C = R >> RHO;
@@ -82,6 +84,7 @@ struct GroupPasses {
       });
     }
     compute<PL, RHO>(v, tid, jg, twp, tw0);
+    if constexpr (S == 0) first_write();
     if constexpr (PL + RHO == LS) {
       if constexpr (SYNC_OUT && S > 0) sync();
       static_for<0, C>([&](auto c_) {
@@ -103,7 +106,7 @@ struct GroupPasses {
         });
       });
       sync();
-      run<SYNC_OUT, S + 1>(v, tid, jg, twp, tw0, xw, xr, sync, out);
+      run<SYNC_OUT, S + 1>(v, tid, jg, twp, tw0, xw, xr, sync, out, first_write);
     }
   }
 };

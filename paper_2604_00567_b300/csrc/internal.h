@@ -68,6 +68,16 @@ FusedShape fused_shape(int prec, int log2n, bool narrow = false);
 bool fused_has_narrow(int prec, int log2n);
 cudaError_t prepare_fused(int prec, int log2n, bool narrow = false);
 
+// Persistent fused kernel fed by bulk copies (fused_tma.cu), 2^8 <= N <=
+// 2^14 (FP32: 2^13).  `grid`: the resident blocks of the device (prepare_fused_tma);
+// `status`: device word whose bit 0 a block sets when a bounded wait for its
+// copies gives up; `tx_extra` (fault injection, normally 0) is added to the
+// byte count each copy barrier expects.  `in` must be 16-byte aligned.
+constexpr int kFusedTmaMinLog2N = 8;
+bool fused_tma_valid(int prec, int log2n);
+FusedShape fused_tma_shape(int prec, int log2n);
+cudaError_t prepare_fused_tma(int prec, int log2n, int *grid);
+
 // Twiddles of the first register stage (passes 0 .. log2(R)-1, whose j is 0
 // for every thread): the first 2^r - 1 per-pass entries, passed by value so
 // the kernel reads them from the constant bank.
@@ -79,6 +89,10 @@ struct Stage0Twiddles {
 // the device per-pass table, `tw0` its first entries.
 cudaError_t launch_fused(int prec, int log2n, bool narrow, bool scaled, const void *in, void *out, int64_t batch,
                          const uint4 *twp, const Stage0Twiddles &tw0, cudaStream_t stream);
+
+cudaError_t launch_fused_tma(int prec, int log2n, bool scaled, const void *in, void *out, int64_t batch,
+                             const uint4 *twp, const Stage0Twiddles &tw0, int grid, int *status, uint32_t tx_extra,
+                             cudaStream_t stream);
 
 // N > 2^14: two sweeps over HBM (passes [0, ls1) then the rest; ls1 = 0
 // picks ceil(m/2)).  Both sweeps hold 7..12 passes (sweep_ls1_valid).

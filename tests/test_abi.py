@@ -103,12 +103,14 @@ def test_host_side_validation_without_gpu(lib):
     o.autotune = 2
     assert lib.fft_plan_create(ctypes.byref(h), 1024, 0, 2, ctypes.byref(o)) == 1
     o.autotune = 0
-    for n, variant in ((1024, 3), (1024, 4), (1 << 20, 1), (1 << 20, 2), (1 << 18, 3), (1 << 17, 3), (8, 2)):
+    for n, variant in ((1024, 3), (1024, 4), (1 << 20, 1), (1 << 20, 2), (1 << 18, 3), (1 << 17, 3), (8, 2),
+                       (128, 5), (1 << 14, 5), (1 << 15, 5)):
         o.variant = variant   # a variant the size does not have (FP32)
         assert lib.fft_plan_create(ctypes.byref(h), n, 0, 2, ctypes.byref(o)) == 3, (n, variant)
     assert lib.fft_exec(None, None, None, 1, -1, None) == 1
     assert lib.fft_plan_destroy(None) == 0
     assert lib.fft_plan_get_info(None, None) == 1
+    assert lib.fft_plan_device_status(None) == 1
     assert lib.fft_plan_get_table(None, -1, None, 0) == 1
     assert lib.fft_plan_get_table4(None, -1, None, 0) == 1
     assert lib.fft_status_string(2).decode().startswith("invalid size")

@@ -50,7 +50,7 @@ def test_autotune_and_cache(dsfft, tmp_path, monkeypatch):
     monkeypatch.setenv("DSFFT_AUTOTUNE_CACHE", str(cache))
     p1 = dsfft.Plan(4096, "fp16", "dual_select", autotune=True)
     i1 = p1.info()
-    assert i1["autotuned"] == 1 and i1["variant_name"] in ("fused_wide", "fused_narrow")
+    assert i1["autotuned"] == 1 and i1["variant_name"] in ("fused_wide", "fused_narrow", "fused_tma")
     data = json.loads(cache.read_text())
     keys = [k for k in data if k != "format"]
     assert len(keys) == 1 and keys[0].endswith("|1|12|2") and data[keys[0]] == i1["variant"]
