@@ -156,6 +156,15 @@ __device__ __forceinline__ uint32_t b2_mul(uint32_t a, uint32_t b) {
   return d;
 }
 
+// Exchange the two halves of a packed pair.  Written as an unpack and
+// repack of the 16-bit halves (not a byte permute) so that the compiler can
+// fold it into the operand of the packed FMA that consumes it.
+__device__ __forceinline__ uint32_t swap_halves(uint32_t x) {
+  uint32_t y;
+  asm("{.reg .b16 l, h;\n\tmov.b32 {l, h}, %1;\n\tmov.b32 %0, {h, l};}" : "=r"(y) : "r"(x));
+  return y;
+}
+
 template <int PREC, bool SCALED> struct BflyPacked {
   static __device__ __forceinline__ uint32_t fma2(uint32_t a, uint32_t b, uint32_t c) {
     return PREC == kFP16 ? h2_fma(a, b, c) : b2_fma(a, b, c);
@@ -163,15 +172,25 @@ template <int PREC, bool SCALED> struct BflyPacked {
   static __device__ __forceinline__ uint32_t mul2(uint32_t a, uint32_t b) {
     return PREC == kFP16 ? h2_mul(a, b) : b2_mul(a, b);
   }
+  // fma(-a, b, c): the negation is exact and is written as its own
+  // instruction so that the compiler can fold it into the FMA's operand.
+  static __device__ __forceinline__ uint32_t nfma2(uint32_t a, uint32_t b, uint32_t c) {
+    uint32_t d;
+    if (PREC == kFP16)
+      asm("{.reg .b32 n;\n\tneg.f16x2 n, %1;\n\tfma.rn.f16x2 %0, n, %2, %3;}" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    else
+      asm("{.reg .b32 n;\n\tneg.bf16x2 n, %1;\n\tfma.rn.bf16x2 %0, n, %2, %3;}" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+  }
   static __device__ __forceinline__ void run(uint32_t &a, uint32_t &b, const uint4 e) {
     // X = cosine ? swap(b) : b ; Y = swap(X)
     const uint32_t X = __byte_perm(b, b, e.z);
-    const uint32_t Y = __byte_perm(X, X, 0x1032);
+    const uint32_t Y = swap_halves(X);
     const uint32_t uv = fma2(e.x, X, Y);           // (u, v)
     uint32_t ah = a;
     if (SCALED) ah = mul2(a, PREC == kFP16 ? 0x38003800u : 0x3F003F00u);  // x 0.5
-    a = fma2(e.y, uv, ah);
-    b = fma2(e.w, uv, ah);
+    a = fma2(e.y, uv, ah);                         // (sigma m, m) (u, v) + a
+    b = nfma2(e.y, uv, ah);                        // -(sigma m, m) (u, v) + a
   }
 };
 
@@ -231,8 +250,7 @@ template <int PREC, bool SCALED> struct Bfly4Packed {
   static constexpr uint32_t kQuarter = PREC == kFP16 ? 0x34003400u : 0x3E803E80u;
   static __device__ __forceinline__ uint32_t pre(const uint32_t b, const uint4 e) {
     const uint32_t X = __byte_perm(b, b, e.z);
-    const uint32_t Y = __byte_perm(X, X, 0x1032);
-    return B::fma2(e.x, X, Y);
+    return B::fma2(e.x, X, swap_halves(X));
   }
   // sgn: the half pair (lo s, hi -s) with s = -1 forward, +1 inverse
   static __device__ __forceinline__ void run(uint32_t &a0, uint32_t &a1, uint32_t &a2, uint32_t &a3, const uint4 e1,
@@ -241,9 +259,9 @@ template <int PREC, bool SCALED> struct Bfly4Packed {
     uint32_t x0 = a0;
     if (SCALED) x0 = B::mul2(a0, kQuarter);
     const uint32_t b3 = B::mul2(e3.y, p3);
-    const uint32_t c0 = B::fma2(e2.y, p2, x0), c1 = B::fma2(e2.w, p2, x0);
-    const uint32_t c2 = B::fma2(e1.y, p1, b3), d3 = B::fma2(e1.w, p1, b3);
-    const uint32_t D = __byte_perm(d3, d3, 0x1032);   // (d3i, d3r)
+    const uint32_t c0 = B::fma2(e2.y, p2, x0), c1 = B::nfma2(e2.y, p2, x0);
+    const uint32_t c2 = B::fma2(e1.y, p1, b3), d3 = B::nfma2(e1.y, p1, b3);
+    const uint32_t D = swap_halves(d3);   // (d3i, d3r)
     a0 = B::fma2(c2, kOne, c0);
     a1 = B::fma2(c2, kOne ^ 0x80008000u, c0);
     a2 = B::fma2(D, sgn, c1);
