@@ -95,7 +95,7 @@ int default_variant(int prec, int log2n) {
                                       : (log2n >= 5 && log2n <= 8);
     return narrow && fused_has_narrow(prec, log2n) ? FFT_VARIANT_FUSED_NARROW : FFT_VARIANT_FUSED_WIDE;
   }
-  if (log2n == 15 || (log2n == 16 && prec != kFP32)) return FFT_VARIANT_CLUSTER;
+  if (cluster_log2k(prec, log2n) >= 0) return FFT_VARIANT_CLUSTER;   // 2^15..2^17 (FP32 2^16)
   return FFT_VARIANT_SWEEPS;
 }
 

@@ -5,29 +5,30 @@
 // [LS1, m)), but the intermediate Stockham array Z_LS1 lives in the
 // cluster's distributed shared memory instead of HBM:
 //   phase 1: CTA `rank` runs passes [0, LS1) on groups g = rank GC1 + lg
-//            (values x[g + q M2], q in [0, M1)) and keeps Z_LS1[g M1 + o]
-//            in its own shared memory;
-//   cluster barrier;
+//            (values x[g + q M2], q in [0, M1)); its last register stage
+//            stores each output Z_LS1[g M1 + o] straight into the shared
+//            memory of the CTA that needs it in phase 2 (DSMEM stores:
+//            value g of phase-2 group o, owner o / GC2);
 //   phase 2: CTA `rank` reads, for groups g' = rank GC2 + lg, the values
-//            Z_LS1[g' + q M1] (q in [0, M2)) from the shared memory of CTA
-//            q / GC1 (DSMEM loads), runs passes [LS1, m) and stores
-//            X[g' + o M1] to HBM.
-// A second cluster barrier separates the remote reads from the reuse of the
-// buffer for phase 2's own exchanges (and from the owner's exit); it is
-// split: each thread arrives once its remote reads are done and waits only
-// before its first write to the buffer, so the first register stage of
-// phase 2 runs while the other CTAs finish their reads.  Every radix-2 butterfly of the
-// pass-by-pass algorithm is executed with its own operands and twiddle, so
-// the output is bit-identical to it; HBM sees one read and one write.
+//            Z_LS1[g' + q M1] (q in [0, M2)) from its own shared memory,
+//            runs passes [LS1, m) and stores X[g' + o M1] to HBM.
+// Two cluster barriers: (A) no CTA writes into another before that CTA has
+// read its last phase-1 exchange (split: each thread arrives once it has
+// read, computes its last phase-1 stage, and waits just before its remote
+// stores); (B) every remote store has landed before phase 2 reads.  After
+// (B) no CTA touches another's memory, so a CTA may exit as soon as it is
+// done.  Every radix-2 butterfly of the pass-by-pass algorithm is executed
+// with its own operands and twiddle, so the output is bit-identical to it;
+// HBM sees one read and one write.
 //
-// Shared layout (both phases): value o of local group lg at lg (M + 1) + o,
-// M the group length (one pad element per group).  Lanes of a warp are
-// consecutive groups: their local accesses (same o) fall in distinct banks,
-// every access is a per-thread base plus a compile-time offset, and the
-// phase-2 remote reads (same phase-1 group q, consecutive o = g') cover 32
-// consecutive elements of the owner's memory.  The first register stage of
-// phase 1 (passes 0..4, the same twiddles for every thread) reads its
-// twiddles from the kernel parameters (constant bank).
+// Shared layout: value o of local group lg at lg (M + 1) + o, M the group
+// length (one pad element per group).  Lanes of a warp are consecutive
+// groups: their local accesses (same o) fall in distinct banks, every access
+// is a per-thread base plus a compile-time offset, and the remote stores of
+// a warp (same output o, consecutive g) fill 32 consecutive elements of one
+// owner's group.  The first register stage of phase 1 (passes 0..4, the
+// same twiddles for every thread) reads its twiddles from the kernel
+// parameters (constant bank).
 #include <cooperative_groups.h>
 
 #include "group.cuh"
@@ -43,18 +44,11 @@ __device__ __forceinline__ void cl_stcs(float2 *p, float2 v) { __stcs(p, v); }
 __device__ __forceinline__ void cl_stcs(uint32_t *p, uint32_t v) { __stcs(reinterpret_cast<unsigned int *>(p), v); }
 
 // Distributed shared memory: map a local shared address into CTA `rank`'s
-// window and load from it.  Volatile: the loads must stay between the two
-// cluster barriers.
+// window.
 __device__ __forceinline__ uint32_t dsmem_map(uint32_t local_addr, uint32_t rank) {
   uint32_t r;
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local_addr), "r"(rank));
   return r;
-}
-__device__ __forceinline__ void dsmem_ld(uint32_t addr, uint32_t &v) {
-  asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
-}
-__device__ __forceinline__ void dsmem_ld(uint32_t addr, float2 &v) {
-  asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr) : "memory");
 }
 
 template <int PREC, int LOG2N, int LOG2K, bool SCALED>
@@ -79,8 +73,20 @@ struct Clus {
   static_assert(GC2 * P2::T == TPB, "both phases use the same threads");
   static_assert(GC1 >= 32 && GC2 >= 32, "a warp must span 32 groups");
   static_assert(K <= 8, "portable cluster size");
-  static_assert(GC1 % P2::T == 0, "a thread's phase-2 reads never straddle two owners");
+  static_assert(LS1 > P1::LOG2R, "phase 1 has an exchange before its last stage");
+  static_assert(GC2 >= (1 << (((LS1 - 1) / P1::LOG2R) * P1::LOG2R)),
+                "a phase-1 output's owner depends only on its compile-time part");
 };
+
+// Remote stores (volatile: they must stay between the two cluster barriers).
+__device__ __forceinline__ void dsmem_st(uint32_t addr, uint32_t v) {
+  asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+__device__ __forceinline__ void dsmem_st(uint32_t addr, float2 v) {
+  asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(v.x), "f"(v.y) : "memory");
+}
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
 
 template <int PREC, int LOG2N, int LOG2K, bool SCALED, class IO>
 __global__ void __cluster_dims__(1 << LOG2K, 1, 1)
@@ -94,58 +100,62 @@ __global__ void __cluster_dims__(1 << LOG2K, 1, 1)
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   const int64_t tr = (int64_t)blockIdx.x / K::K;
-  // the grid is exactly batch * K blocks, so every cluster is active
   (void)batch;
   auto tw0f = [&](int i) { return tw0.e[i]; };
+  constexpr int ES = (int)sizeof(E);
 
   E v[K::R];
-  // ---- phase 1: passes [0, LS1) ----
+  // ---- phase 1: passes [0, LS1); outputs pushed into the owners' phase-2 layout ----
   {
     const int lg = threadIdx.x % K::GC1;
     const int tid = threadIdx.x / K::GC1;
-    const int64_t g = (int64_t)rank * K::GC1 + lg;
+    const int g = rank * K::GC1 + lg;
     const E *src = io.src(tr) + g;
     static_for<0, K::R>([&](auto p_) {
       constexpr int p = decltype(p_)::value;
       v[p] = cl_ldcs(src + (int64_t)(tid + p * K::P1::T) * K::M2);
     });
+    // output o = a + b (a = tid + c T1 runtime, b compile-time) is Z_LS1[g M1 + o]:
+    // value g of phase-2 group o, held by CTA o / GC2 at local group o mod GC2
+    const uint32_t pbase = (uint32_t)__cvta_generic_to_shared(sm) + (uint32_t)((tid * K::S2 + g) * ES);
+    uint32_t rbase[K::K];
+    static_for<0, K::K>([&](auto r_) { rbase[decltype(r_)::value] = dsmem_map(pbase, decltype(r_)::value); });
     E *grp = sm + lg * K::S1;
-    K::P1::template run<true>(
+    K::P1::template run<false>(
         v, tid, 0, twp, tw0f, [&](int idx, E val) { grp[idx] = val; }, [&](int idx) { return grp[idx]; },
-        [] { __syncthreads(); }, [&](int o, E val) { grp[o] = val; }, [] {});
+        [] { __syncthreads(); },
+        [&](int a, auto b_, E val) {
+          constexpr int b = decltype(b_)::value;
+          constexpr int owner = b / K::GC2;
+          constexpr int lgo = b % K::GC2;
+          // a = tid + c T1: the c T1 part is folded by the caller into `a`; recover it
+          dsmem_st(rbase[owner] + (uint32_t)(((a - tid) + lgo) * K::S2 * ES), val);
+        },
+        [] {}, [] { cluster_arrive(); }, [] { cluster_wait(); });
   }
-  cluster.sync();   // Z_LS1 complete in every CTA of the cluster
-  // ---- phase 2: passes [LS1, m) ----
+  cluster_arrive();   // every push done (release) ...
+  cluster_wait();     // ... and visible before phase 2 reads them
+  // ---- phase 2: passes [LS1, m) from local shared memory ----
   {
-    // opaque copy of the thread index: stops the compiler from sharing
-    // phase 1's address arithmetic (and keeping it live) when GC1 == GC2
     unsigned tx;
     asm volatile("mov.u32 %0, %%tid.x;" : "=r"(tx));
     const int lg = tx % K::GC2;
     const int tid = tx / K::GC2;
     const int gp = rank * K::GC2 + lg;          // g' in [0, M1)
-    // Z_LS1[g' + q M1] is value o = g' of phase-1 group q, held by CTA
-    // q / GC1 at local group q mod GC1; with q = tid + p T2 and T2 | GC1 the
-    // owner and the group's offset are compile-time for each p
-    const uint32_t local_base =
-        (uint32_t)__cvta_generic_to_shared(sm) + (uint32_t)((tid * K::S1 + gp) * (int)sizeof(E));
-    uint32_t rbase[K::K];
-    static_for<0, K::K>([&](auto r_) { rbase[decltype(r_)::value] = dsmem_map(local_base, decltype(r_)::value); });
+    E *grp = sm + lg * K::S2;
     static_for<0, K::R>([&](auto p_) {
       constexpr int p = decltype(p_)::value;
-      constexpr int owner = (p * K::P2::T) / K::GC1;
-      constexpr int gl0 = (p * K::P2::T) % K::GC1;
-      dsmem_ld(rbase[owner] + (uint32_t)(gl0 * K::S1 * (int)sizeof(E)), v[p]);
+      v[p] = grp[tid + p * K::P2::T];
     });
-    // arrive: this thread's remote reads are done (release orders them
-    // first); wait: every CTA's reads of this buffer are done
-    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
-    E *grp = sm + lg * K::S2;
     E *dst = io.dst(tr) + gp;
     K::P2::template run<false>(
         v, tid, gp, twp, tw0f, [&](int idx, E val) { grp[idx] = val; }, [&](int idx) { return grp[idx]; },
-        [] { __syncthreads(); }, [&](int o, E val) { cl_stcs(dst + (int64_t)o * K::M1, val); },
-        [] { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); });
+        [] { __syncthreads(); },
+        [&](int a, auto b_, E val) {
+          constexpr int b = decltype(b_)::value;
+          cl_stcs(dst + (int64_t)(a + b) * K::M1, val);
+        },
+        [] { __syncthreads(); }, [] {}, [] {});
   }
 }
 

@@ -70,28 +70,33 @@ struct GroupPasses {
   // SYNC_OUT the block synchronises before the outputs (when out() writes
   // the exchange buffer).  first_write() runs once, after the first register
   // stage and before the first write to the exchange buffer or output.
-  template <bool SYNC_OUT = false, int S = 0, class TW0, class XW, class XR, class SYNC, class OUT, class FW>
+  template <bool SYNC_OUT = false, int S = 0, class TW0, class XW, class XR, class SYNC, class OUT, class FW,
+            class PR, class PO>
   static __device__ __forceinline__ void run(E (&v)[R], int tid, int jg, const uint4 *__restrict__ twp,
                                              const TW0 &tw0, XW &&xw, XR &&xr, SYNC &&sync, OUT &&out,
-                                             FW &&first_write) {
+                                             FW &&first_write, PR &&post_read, PO &&pre_out) {
     constexpr int PL = S * LOG2R;
     constexpr int RHO = (LS - PL) < LOG2R ? (LS - PL) : LOG2R;
     constexpr int C = R >> RHO;
+    constexpr bool LAST = PL + RHO == LS;
     if constexpr (S > 0) {
       static_for<0, R>([&](auto p_) {
         constexpr int p = decltype(p_)::value;
         v[p] = xr(tid + p * T);
       });
+      if constexpr (LAST) post_read();
     }
     compute<PL, RHO>(v, tid, jg, twp, tw0);
     if constexpr (S == 0) first_write();
-    if constexpr (PL + RHO == LS) {
+    if constexpr (LAST) {
       if constexpr (SYNC_OUT && S > 0) sync();
+      pre_out();
       static_for<0, C>([&](auto c_) {
         constexpr int c = decltype(c_)::value;
         static_for<0, (1 << RHO)>([&](auto q_) {
           constexpr int q = decltype(q_)::value;
-          out(tid + c * T + (bitrev(q, RHO) << PL), v[c + q * C]);
+          // local output o = (tid + c T) + (bitrev(q) << PL), tid + c T < 2^PL
+          out(tid + c * T, std::integral_constant<int, (bitrev(q, RHO) << PL)>{}, v[c + q * C]);
         });
       });
     } else {
@@ -106,7 +111,7 @@ struct GroupPasses {
         });
       });
       sync();
-      run<SYNC_OUT, S + 1>(v, tid, jg, twp, tw0, xw, xr, sync, out, first_write);
+      run<SYNC_OUT, S + 1>(v, tid, jg, twp, tw0, xw, xr, sync, out, first_write, post_read, pre_out);
     }
   }
 };

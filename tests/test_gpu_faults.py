@@ -75,6 +75,7 @@ def test_other_creators_oom(dsfft, fault):
 @pytest.mark.parametrize("prec,log2n,variant,radix", [
     ("fp16", 5, "auto", 2), ("fp16", 10, "auto", 2), ("fp32", 12, "fused_narrow", 2), ("bf16", 14, "auto", 2),
     ("fp16", 15, "cluster", 2), ("fp16", 16, "cluster", 2), ("fp32", 16, "sweeps", 2), ("fp16", 17, "sweeps", 2),
+    ("fp16", 17, "cluster", 2), ("fp32", 16, "cluster", 2), ("fp32", 15, "cluster", 2),
     ("fp16", 11, "auto", 4), ("fp32", 16, "auto", 4)])
 def test_guard_bands_untouched(dsfft, prec, log2n, variant, radix):
     """The output lies between two guard transforms filled with a pattern;

@@ -19,9 +19,9 @@ def dsfft():
 
 
 def _expected_kernel(prec, log2n):
-    """Built-in choice (measured on B300): the cluster (DSMEM) kernel for
-    2^15 and, for FP16/BF16, 2^16; two HBM sweeps above."""
-    return 2 if log2n == 15 or (log2n == 16 and prec != "fp32") else 1
+    """Built-in choice (measured on B300): the cluster (DSMEM) kernel up to
+    2^16 (FP32) / 2^17 (FP16, BF16); two HBM sweeps above."""
+    return 2 if log2n <= (16 if prec == "fp32" else 17) else 1
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp16", "bf16"])
