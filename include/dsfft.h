@@ -211,9 +211,10 @@ DSFFT_API fft_status fft_plan_get_table(const fft_plan *plan, fft_direction dir,
 DSFFT_API fft_status fft_plan_get_table4(const fft_plan *plan, fft_direction dir, void *host_dst, size_t bytes);
 
 /* Read and clear the plan's device error word.  Kernels whose waits are
- * bounded (the FFT_VARIANT_FUSED_TMA kernel waits at most about one second
- * for each bulk copy) set it when such a wait gives up; the affected blocks
- * then skip their remaining transforms, so the output is incomplete.
+ * bounded set it when such a wait gives up (about one second): the
+ * FFT_VARIANT_FUSED_TMA kernel waiting for a bulk copy (bit 0), the 8-CTA
+ * FP16/BF16 cluster kernel waiting for its phase-1 data (bit 1); the
+ * affected blocks skip their remaining work, so the output is incomplete.
  * Returns FFT_ERR_TIMEOUT if it was set since the last call, else FFT_OK.
  * Synchronous: waits for all work queued on the plan's device first. */
 DSFFT_API fft_status fft_plan_device_status(const fft_plan *plan);

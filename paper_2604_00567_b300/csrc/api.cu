@@ -146,7 +146,8 @@ cudaError_t plan_launch(const fft_plan *p, const void *in, void *out, int64_t ba
   if (p->kernel == 0)
     return launch_fused(p->prec, p->log2n, p->narrow, scaled, in, out, batch, p->twp[d], p->tw0[d], stream);
   if (p->kernel == 2)
-    return launch_cluster(p->prec, p->log2n, scaled, in, out, nullptr, batch, p->twp[d], p->tw0[d], stream);
+    return launch_cluster(p->prec, p->log2n, scaled, in, out, nullptr, batch, p->twp[d], p->tw0[d], p->status,
+                          stream);
   return launch_sweeps(p->prec, p->log2n, scaled, in, out, nullptr, batch, p->twp[d], stream, p->sweep_ls1);
 }
 
@@ -310,6 +311,7 @@ bool dsfft::plan_view(const fft_plan *p, PlanView *v) {
   v->tw0[1] = &p->tw0[1];
   v->radix = p->radix;
   v->sweep_ls1 = p->sweep_ls1;
+  v->status = p->status;
   return true;
 }
 
@@ -371,7 +373,7 @@ cudaError_t batch_enqueue(const fft_batch *b, cudaStream_t stream) {
     const bool scaled = p->scale[g.dir] != 0;
     if (p->kernel == 2)
       e = launch_cluster(p->prec, p->log2n, scaled, nullptr, nullptr, b->d_items + g.first, g.count, p->twp[g.dir],
-                         p->tw0[g.dir], stream);
+                         p->tw0[g.dir], p->status, stream);
     else
       e = launch_sweeps(p->prec, p->log2n, scaled, nullptr, nullptr, b->d_items + g.first, g.count, p->twp[g.dir],
                         stream, p->sweep_ls1);

@@ -12,12 +12,15 @@
 //   phase 2: CTA `rank` reads, for groups g' = rank GC2 + lg, the values
 //            Z_LS1[g' + q M1] (q in [0, M2)) from its own shared memory,
 //            runs passes [LS1, m) and stores X[g' + o M1] to HBM.
-// Two cluster barriers: (A) no CTA writes into another before that CTA has
-// read its last phase-1 exchange (split: each thread arrives once it has
-// read, computes its last phase-1 stage, and waits just before its remote
-// stores); (B) every remote store has landed before phase 2 reads.  After
-// (B) no CTA touches another's memory, so a CTA may exit as soon as it is
-// done.  Every radix-2 butterfly of the pass-by-pass algorithm is executed
+// Cluster barrier (A): no CTA writes into another before that CTA has read
+// its last phase-1 exchange (split: each thread arrives once it has read,
+// computes its last phase-1 stage, and waits just before its remote
+// stores).  Then (B), every remote store has landed before phase 2 reads:
+// for 4-byte elements in 8-CTA clusters the stores are st.async and each
+// CTA waits (bounded) on its own mbarrier until its phase-2 bytes have
+// arrived, with a relaxed cluster arrive after the stores and the matching
+// wait at exit so that no CTA leaves while another may still send to it;
+// otherwise plain remote stores and a second cluster barrier.  Every radix-2 butterfly of the pass-by-pass algorithm is executed
 // with its own operands and twiddle, so the output is bit-identical to it;
 // HBM sees one read and one write.
 //
@@ -70,6 +73,10 @@ struct Clus {
   static constexpr int S2 = M2 + 1;
   static constexpr int SMEM = (GC1 * S1 > GC2 * S2 ? GC1 * S1 : GC2 * S2) * (int)sizeof(E);
   static constexpr int MINB = TPB >= 1024 ? 1 : 1024 / TPB;   // 1024 resident threads: <= 64 registers
+  // Phase-1 outputs by st.async counted on the owner's mbarrier (measured
+  // faster on B300 for 4-byte elements in 8-CTA clusters), else by plain
+  // remote stores and a second cluster barrier.
+  static constexpr bool ASYNC = PREC != kFP32 && LOG2K == 3;
   static_assert(GC2 * P2::T == TPB, "both phases use the same threads");
   static_assert(GC1 >= 32 && GC2 >= 32, "a warp must span 32 groups");
   static_assert(K <= 8, "portable cluster size");
@@ -77,6 +84,41 @@ struct Clus {
   static_assert(GC2 >= (1 << (((LS1 - 1) / P1::LOG2R) * P1::LOG2R)),
                 "a phase-1 output's owner depends only on its compile-time part");
 };
+
+// Asynchronous remote stores whose arrival the destination CTA counts on
+// its own mbarrier (complete_tx, in bytes), and the bounded wait on it.
+__device__ __forceinline__ void st_async(uint32_t addr, uint32_t v, uint32_t bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(addr), "r"(v),
+               "r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void st_async(uint32_t addr, float2 v, uint32_t bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];" ::"r"(addr),
+               "f"(v.x), "f"(v.y), "r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint32_t bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// false after about one second (%globaltimer)
+__device__ __forceinline__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity) {
+  if (mbar_try_wait_cluster(bar, parity)) return true;
+  uint64_t t0, t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  for (;;) {
+    if (mbar_try_wait_cluster(bar, parity)) return true;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    if (t - t0 > 1000000000ull) return false;
+  }
+}
 
 // Remote stores (volatile: they must stay between the two cluster barriers).
 __device__ __forceinline__ void dsmem_st(uint32_t addr, uint32_t v) {
@@ -87,12 +129,15 @@ __device__ __forceinline__ void dsmem_st(uint32_t addr, float2 v) {
 }
 __device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
 __device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cluster_arrive_relaxed() {
+  asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+}
 
 template <int PREC, int LOG2N, int LOG2K, bool SCALED, class IO>
 __global__ void __cluster_dims__(1 << LOG2K, 1, 1)
     __launch_bounds__(Clus<PREC, LOG2N, LOG2K, SCALED>::TPB, Clus<PREC, LOG2N, LOG2K, SCALED>::MINB)
     cluster_fft_kernel(const IO io, int64_t batch, const uint4 *__restrict__ twp,
-                       const __grid_constant__ Stage0Twiddles tw0) {
+                       const __grid_constant__ Stage0Twiddles tw0, int *status) {
   using K = Clus<PREC, LOG2N, LOG2K, SCALED>;
   using E = typename K::E;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -103,6 +148,19 @@ __global__ void __cluster_dims__(1 << LOG2K, 1, 1)
   (void)batch;
   auto tw0f = [&](int i) { return tw0.e[i]; };
   constexpr int ES = (int)sizeof(E);
+
+  // ASYNC: completes when this CTA's phase-2 input has arrived (armed with
+  // its byte count; initialised before cluster barrier A, which every
+  // sender passes before its first store)
+  __shared__ __align__(8) uint64_t recv_bar;
+  const uint32_t bar_local = (uint32_t)__cvta_generic_to_shared(&recv_bar);
+  if (K::ASYNC && threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_local) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_local),
+                 "r"((uint32_t)(K::GC2 * K::M2 * ES))
+                 : "memory");
+  }
 
   E v[K::R];
   // ---- phase 1: passes [0, LS1); outputs pushed into the owners' phase-2 layout ----
@@ -118,8 +176,11 @@ __global__ void __cluster_dims__(1 << LOG2K, 1, 1)
     // output o = a + b (a = tid + c T1 runtime, b compile-time) is Z_LS1[g M1 + o]:
     // value g of phase-2 group o, held by CTA o / GC2 at local group o mod GC2
     const uint32_t pbase = (uint32_t)__cvta_generic_to_shared(sm) + (uint32_t)((tid * K::S2 + g) * ES);
-    uint32_t rbase[K::K];
-    static_for<0, K::K>([&](auto r_) { rbase[decltype(r_)::value] = dsmem_map(pbase, decltype(r_)::value); });
+    uint32_t rbase[K::K], rbar[K::K];
+    static_for<0, K::K>([&](auto r_) {
+      rbase[decltype(r_)::value] = dsmem_map(pbase, decltype(r_)::value);
+      if constexpr (K::ASYNC) rbar[decltype(r_)::value] = dsmem_map(bar_local, decltype(r_)::value);
+    });
     E *grp = sm + lg * K::S1;
     K::P1::template run<false>(
         v, tid, 0, twp, tw0f, [&](int idx, E val) { grp[idx] = val; }, [&](int idx) { return grp[idx]; },
@@ -129,14 +190,22 @@ __global__ void __cluster_dims__(1 << LOG2K, 1, 1)
           constexpr int owner = b / K::GC2;
           constexpr int lgo = b % K::GC2;
           // a = tid + c T1: the c T1 part is folded by the caller into `a`; recover it
-          dsmem_st(rbase[owner] + (uint32_t)(((a - tid) + lgo) * K::S2 * ES), val);
+          const uint32_t addr = rbase[owner] + (uint32_t)(((a - tid) + lgo) * K::S2 * ES);
+          if constexpr (K::ASYNC) st_async(addr, val, rbar[owner]);
+          else dsmem_st(addr, val);
         },
         [] {}, [] { cluster_arrive(); }, [] { cluster_wait(); });
   }
-  cluster_arrive();   // every push done (release) ...
-  cluster_wait();     // ... and visible before phase 2 reads them
+  bool ok = true;
+  if constexpr (K::ASYNC) {
+    cluster_arrive_relaxed();   // lifetime only: no CTA exits before every CTA has sent
+    ok = mbar_wait_cluster(bar_local, 0);
+  } else {
+    cluster_arrive();   // every remote store done (release) ...
+    cluster_wait();     // ... and visible before phase 2 reads them
+  }
   // ---- phase 2: passes [LS1, m) from local shared memory ----
-  {
+  if (!K::ASYNC || !__syncthreads_or(!ok)) {
     unsigned tx;
     asm volatile("mov.u32 %0, %%tid.x;" : "=r"(tx));
     const int lg = tx % K::GC2;
@@ -156,7 +225,10 @@ __global__ void __cluster_dims__(1 << LOG2K, 1, 1)
           cl_stcs(dst + (int64_t)(a + b) * K::M1, val);
         },
         [] { __syncthreads(); }, [] {}, [] {});
+  } else if (threadIdx.x == 0) {
+    atomicOr(status, 2);   // the input did not arrive in time: this CTA's outputs are not written
   }
+  if constexpr (K::ASYNC) cluster_wait();
 }
 
 // ---------------------------------------------------------------------------
@@ -172,17 +244,18 @@ int cluster_log2k(int prec, int log2n) {
 
 template <int PREC, int LOG2N, int LOG2K, bool SCALED>
 static cudaError_t launch_cluster_one(const void *in, void *out, const BatchItem *items, int64_t batch,
-                                      const uint4 *twp, const Stage0Twiddles &tw0, cudaStream_t stream) {
+                                      const uint4 *twp, const Stage0Twiddles &tw0, int *status,
+                                      cudaStream_t stream) {
   using K = Clus<PREC, LOG2N, LOG2K, SCALED>;
   using E = typename K::E;
   const int64_t blocks = batch * K::K;
   if (blocks > 0x7FFFFFFF) return cudaErrorInvalidConfiguration;
   if (items) {
     cluster_fft_kernel<PREC, LOG2N, LOG2K, SCALED, GatherIO<E>><<<(unsigned)blocks, K::TPB, K::SMEM, stream>>>(
-        GatherIO<E>{items}, batch, twp, tw0);
+        GatherIO<E>{items}, batch, twp, tw0, status);
   } else {
     cluster_fft_kernel<PREC, LOG2N, LOG2K, SCALED, ContigIO<E>><<<(unsigned)blocks, K::TPB, K::SMEM, stream>>>(
-        ContigIO<E>{static_cast<const E *>(in), static_cast<E *>(out), K::N}, batch, twp, tw0);
+        ContigIO<E>{static_cast<const E *>(in), static_cast<E *>(out), K::N}, batch, twp, tw0, status);
   }
   return cudaGetLastError();
 }
@@ -220,11 +293,13 @@ cudaError_t prepare_cluster(int prec, int log2n) {
 }
 
 cudaError_t launch_cluster(int prec, int log2n, bool scaled, const void *in, void *out, const BatchItem *items,
-                           int64_t batch, const uint4 *twp, const Stage0Twiddles &tw0, cudaStream_t stream) {
+                           int64_t batch, const uint4 *twp, const Stage0Twiddles &tw0, int *status,
+                           cudaStream_t stream) {
+  if (!status) return cudaErrorInvalidValue;
 #define DSFFT_CL(P, L, LK)                                                                                 \
   case P * 100 + L:                                                                                        \
-    return scaled ? launch_cluster_one<P, L, LK, true>(in, out, items, batch, twp, tw0, stream)   \
-                  : launch_cluster_one<P, L, LK, false>(in, out, items, batch, twp, tw0, stream);
+    return scaled ? launch_cluster_one<P, L, LK, true>(in, out, items, batch, twp, tw0, status, stream)   \
+                  : launch_cluster_one<P, L, LK, false>(in, out, items, batch, twp, tw0, status, stream);
   switch (prec * 100 + log2n) {
     DSFFT_CL(kFP32, 15, 2)
     DSFFT_CL(kFP32, 16, 3)

@@ -119,8 +119,11 @@ cudaError_t launch_sweeps4(int prec, int log2n, bool scaled, int inverse, const 
 int cluster_log2k(int prec, int log2n);
 cudaError_t prepare_cluster(int prec, int log2n);
 // `tw0`: the first per-pass entries (the fused kernel's stage-0 twiddles).
+// `status`: device word whose bit 1 a CTA sets when its bounded wait for
+// the phase-1 data gives up (the 8-CTA FP16/BF16 kernels).
 cudaError_t launch_cluster(int prec, int log2n, bool scaled, const void *in, void *out, const BatchItem *items,
-                           int64_t batch, const uint4 *twp, const Stage0Twiddles &tw0, cudaStream_t stream);
+                           int64_t batch, const uint4 *twp, const Stage0Twiddles &tw0, int *status,
+                           cudaStream_t stream);
 
 // Read-only view of a plan's launch parameters (for entry points outside
 // api.cu); false for a null plan.
@@ -131,6 +134,7 @@ struct PlanView {
   const Stage0Twiddles *tw0[2];   // host copies of the first per-pass entries
   int radix;                      // 2 or 4
   int sweep_ls1;                  // passes in sweep 1 (0: ceil(m/2))
+  int *status;                    // device error word of the bounded waits
 };
 
 // Host-side trace range around a library call (NVTX: visible in Nsight
