@@ -42,7 +42,7 @@ struct fft_plan {
   Stage0R4 s0r4[2];     // radix-4: first-stage twiddles (host copy)
   int sweep_ls1;        // sweeps: passes in sweep 1 (0: ceil(m/2))
   int tma_grid;         // fused_tma: resident blocks of the device
-  uint32_t tma_tx_extra;  // fused_tma: fault injection (DSFFT_FAULT_TMA_WAIT), else 0
+  uint32_t fault_tx;     // fault injection (DSFFT_FAULT_WAIT): extra bytes each bounded copy wait expects, else 0
   int *status;          // device error word of the bounded waits
 };
 
@@ -142,12 +142,12 @@ cudaError_t plan_launch(const fft_plan *p, const void *in, void *out, int64_t ba
   }
   if (p->variant == FFT_VARIANT_FUSED_TMA && ((uintptr_t)in & 15) == 0)
     return launch_fused_tma(p->prec, p->log2n, scaled, in, out, batch, p->twp[d], p->tw0[d], p->tma_grid, p->status,
-                            p->tma_tx_extra, stream);
+                            p->fault_tx, stream);
   if (p->kernel == 0)
     return launch_fused(p->prec, p->log2n, p->narrow, scaled, in, out, batch, p->twp[d], p->tw0[d], stream);
   if (p->kernel == 2)
     return launch_cluster(p->prec, p->log2n, scaled, in, out, nullptr, batch, p->twp[d], p->tw0[d], p->status,
-                          stream);
+                          p->fault_tx, stream);
   return launch_sweeps(p->prec, p->log2n, scaled, in, out, nullptr, batch, p->twp[d], stream, p->sweep_ls1);
 }
 
@@ -312,6 +312,7 @@ bool dsfft::plan_view(const fft_plan *p, PlanView *v) {
   v->radix = p->radix;
   v->sweep_ls1 = p->sweep_ls1;
   v->status = p->status;
+  v->fault_tx = p->fault_tx;
   return true;
 }
 
@@ -373,7 +374,7 @@ cudaError_t batch_enqueue(const fft_batch *b, cudaStream_t stream) {
     const bool scaled = p->scale[g.dir] != 0;
     if (p->kernel == 2)
       e = launch_cluster(p->prec, p->log2n, scaled, nullptr, nullptr, b->d_items + g.first, g.count, p->twp[g.dir],
-                         p->tw0[g.dir], p->status, stream);
+                         p->tw0[g.dir], p->status, p->fault_tx, stream);
     else
       e = launch_sweeps(p->prec, p->log2n, scaled, nullptr, nullptr, b->d_items + g.first, g.count, p->twp[g.dir],
                         stream, p->sweep_ls1);
@@ -482,7 +483,7 @@ fft_status fft_plan_create(fft_plan **plan, int64_t n, fft_precision prec, fft_f
   p->scale[1] = opts.scale_inverse;
   p->device = device;
   p->radix = radix;
-  if (const char *f = getenv("DSFFT_FAULT_TMA_WAIT")) p->tma_tx_extra = atoi(f) > 0 ? 16u : 0u;
+  if (const char *f = getenv("DSFFT_FAULT_WAIT")) p->fault_tx = atoi(f) > 0 ? 16u : 0u;
 
   const size_t entries = (size_t)(n / 2);
   // per-pass tables hold the compact 8-byte entries for FP16/BF16

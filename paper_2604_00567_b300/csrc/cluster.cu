@@ -137,7 +137,7 @@ template <int PREC, int LOG2N, int LOG2K, bool SCALED, class IO>
 __global__ void __cluster_dims__(1 << LOG2K, 1, 1)
     __launch_bounds__(Clus<PREC, LOG2N, LOG2K, SCALED>::TPB, Clus<PREC, LOG2N, LOG2K, SCALED>::MINB)
     cluster_fft_kernel(const IO io, int64_t batch, const uint4 *__restrict__ twp,
-                       const __grid_constant__ Stage0Twiddles tw0, int *status) {
+                       const __grid_constant__ Stage0Twiddles tw0, int *status, uint32_t tx_extra) {
   using K = Clus<PREC, LOG2N, LOG2K, SCALED>;
   using E = typename K::E;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -158,7 +158,7 @@ __global__ void __cluster_dims__(1 << LOG2K, 1, 1)
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_local) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_local),
-                 "r"((uint32_t)(K::GC2 * K::M2 * ES))
+                 "r"((uint32_t)(K::GC2 * K::M2 * ES) + tx_extra)
                  : "memory");
   }
 
@@ -245,17 +245,17 @@ int cluster_log2k(int prec, int log2n) {
 template <int PREC, int LOG2N, int LOG2K, bool SCALED>
 static cudaError_t launch_cluster_one(const void *in, void *out, const BatchItem *items, int64_t batch,
                                       const uint4 *twp, const Stage0Twiddles &tw0, int *status,
-                                      cudaStream_t stream) {
+                                      uint32_t tx_extra, cudaStream_t stream) {
   using K = Clus<PREC, LOG2N, LOG2K, SCALED>;
   using E = typename K::E;
   const int64_t blocks = batch * K::K;
   if (blocks > 0x7FFFFFFF) return cudaErrorInvalidConfiguration;
   if (items) {
     cluster_fft_kernel<PREC, LOG2N, LOG2K, SCALED, GatherIO<E>><<<(unsigned)blocks, K::TPB, K::SMEM, stream>>>(
-        GatherIO<E>{items}, batch, twp, tw0, status);
+        GatherIO<E>{items}, batch, twp, tw0, status, tx_extra);
   } else {
     cluster_fft_kernel<PREC, LOG2N, LOG2K, SCALED, ContigIO<E>><<<(unsigned)blocks, K::TPB, K::SMEM, stream>>>(
-        ContigIO<E>{static_cast<const E *>(in), static_cast<E *>(out), K::N}, batch, twp, tw0, status);
+        ContigIO<E>{static_cast<const E *>(in), static_cast<E *>(out), K::N}, batch, twp, tw0, status, tx_extra);
   }
   return cudaGetLastError();
 }
@@ -294,12 +294,12 @@ cudaError_t prepare_cluster(int prec, int log2n) {
 
 cudaError_t launch_cluster(int prec, int log2n, bool scaled, const void *in, void *out, const BatchItem *items,
                            int64_t batch, const uint4 *twp, const Stage0Twiddles &tw0, int *status,
-                           cudaStream_t stream) {
+                           uint32_t tx_extra, cudaStream_t stream) {
   if (!status) return cudaErrorInvalidValue;
 #define DSFFT_CL(P, L, LK)                                                                                 \
   case P * 100 + L:                                                                                        \
-    return scaled ? launch_cluster_one<P, L, LK, true>(in, out, items, batch, twp, tw0, status, stream)   \
-                  : launch_cluster_one<P, L, LK, false>(in, out, items, batch, twp, tw0, status, stream);
+    return scaled ? launch_cluster_one<P, L, LK, true>(in, out, items, batch, twp, tw0, status, tx_extra, stream)   \
+                  : launch_cluster_one<P, L, LK, false>(in, out, items, batch, twp, tw0, status, tx_extra, stream);
   switch (prec * 100 + log2n) {
     DSFFT_CL(kFP32, 15, 2)
     DSFFT_CL(kFP32, 16, 3)

@@ -120,10 +120,11 @@ int cluster_log2k(int prec, int log2n);
 cudaError_t prepare_cluster(int prec, int log2n);
 // `tw0`: the first per-pass entries (the fused kernel's stage-0 twiddles).
 // `status`: device word whose bit 1 a CTA sets when its bounded wait for
-// the phase-1 data gives up (the 8-CTA FP16/BF16 kernels).
+// the phase-1 data gives up (the 8-CTA FP16/BF16 kernels); `tx_extra`
+// (fault injection, normally 0) is added to the bytes that wait expects.
 cudaError_t launch_cluster(int prec, int log2n, bool scaled, const void *in, void *out, const BatchItem *items,
                            int64_t batch, const uint4 *twp, const Stage0Twiddles &tw0, int *status,
-                           cudaStream_t stream);
+                           uint32_t tx_extra, cudaStream_t stream);
 
 // Read-only view of a plan's launch parameters (for entry points outside
 // api.cu); false for a null plan.
@@ -135,6 +136,7 @@ struct PlanView {
   int radix;                      // 2 or 4
   int sweep_ls1;                  // passes in sweep 1 (0: ceil(m/2))
   int *status;                    // device error word of the bounded waits
+  uint32_t fault_tx;              // fault injection: extra bytes each bounded copy wait expects (normally 0)
 };
 
 // Host-side trace range around a library call (NVTX: visible in Nsight

@@ -34,3 +34,29 @@ def test_cluster_contiguous_vs_gathered(dsfft, prec, log2n):
         assert torch.equal(y[i].view(word), yb[i].view(word)), i
     xs = signals.from_torch(x[batch - 1:batch], prec)
     assert_bitexact(signals.from_torch(y[batch - 1:batch], prec), emulate(plan, xs, -1), f"{prec} 2^{log2n} last")
+    plan.device_status()            # no bounded wait gave up
+
+
+@pytest.mark.parametrize("prec,log2n", [("fp16", 16), ("bf16", 17)])
+def test_cluster_wait_limit_sets_status(dsfft, monkeypatch, prec, log2n):
+    """Fault injection: each CTA's mbarrier expects 16 bytes more than the
+    other CTAs send, so the wait for the phase-1 data runs out (about 1 s);
+    the CTA records it in the plan's status word and skips phase 2, and the
+    cluster still leaves together.  No GPU fault: the context stays usable."""
+    import torch
+    n = 1 << log2n
+    monkeypatch.setenv("DSFFT_FAULT_WAIT", "1")
+    bad = dsfft.Plan(n, prec, "dual_select", variant="cluster")
+    monkeypatch.delenv("DSFFT_FAULT_WAIT")
+    x = signals.device_signal(4, n, prec, seed=7)
+    bad.exec(x)
+    with pytest.raises(dsfft.DsfftError) as e:
+        bad.device_status()
+    assert e.value.status == 6
+    bad.device_status()             # cleared by the read
+    good = dsfft.Plan(n, prec, "dual_select", variant="cluster")
+    y = good.exec(x)
+    torch.cuda.synchronize()
+    xs = signals.from_torch(x[3:4], prec)
+    assert_bitexact(signals.from_torch(y[3:4], prec), emulate(good, xs, -1), "after the injected timeout")
+    good.device_status()

@@ -97,9 +97,9 @@ def test_tma_wait_limit_sets_status(dsfft, monkeypatch):
     block records it in the status word, waits (bounded) for its copies and
     returns.  No GPU fault: the context stays usable."""
     import torch
-    monkeypatch.setenv("DSFFT_FAULT_TMA_WAIT", "1")
+    monkeypatch.setenv("DSFFT_FAULT_WAIT", "1")
     bad = dsfft.Plan(1024, "fp16", "dual_select", variant="fused_tma")
-    monkeypatch.delenv("DSFFT_FAULT_TMA_WAIT")
+    monkeypatch.delenv("DSFFT_FAULT_WAIT")
     x = signals.to_torch(signals.signal(1320, 64, 1024, "fp16"), "fp16", "cuda")
     bad.exec(x)
     with pytest.raises(dsfft.DsfftError) as e:
