@@ -48,7 +48,7 @@ LOG2NS = (10, 12, 14, 16)
 BATCH_BYTES = 1 << 30
 PRECISION = "fp16"
 FACTORIZATION = "dual_select"
-CPU_SAMPLE_DIV = 16          # oracle sample: batch / 16 signals per N (about 10 s on 16 cores)
+CPU_SAMPLE_DIV = 8           # oracle sample: batch / 8 signals per N (about 10 s on 16 cores)
 
 
 def batch_for(log2n: int, precision: str = PRECISION) -> int:
