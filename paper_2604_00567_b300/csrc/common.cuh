@@ -114,15 +114,9 @@ template <> struct Elem<kBF16> { using T = uint32_t; };
 template <int PREC, bool SCALED> struct Bfly;
 
 template <bool SCALED> struct Bfly<kFP32, SCALED> {
-  static __device__ __forceinline__ void run(float2 &a, float2 &b, const uint4 e) {
-    const float t = __uint_as_float(e.x);
+  static __device__ __forceinline__ void finish(float2 &a, float2 &b, const uint4 e, float u, float v) {
     const float m = __uint_as_float(e.y);
     const float sm = __uint_as_float(e.z);
-    const bool sine = e.w != 0u;
-    const float R = sine ? b.y : b.x;
-    const float S = sine ? b.x : b.y;
-    const float u = __fmaf_rn(-t, S, R);
-    const float v = __fmaf_rn(t, R, S);
     float ar = a.x, ai = a.y;
     if (SCALED) {
       ar = __fmul_rn(ar, 0.5f);
@@ -132,6 +126,22 @@ template <bool SCALED> struct Bfly<kFP32, SCALED> {
     b.x = __fmaf_rn(-sm, u, ar);
     a.y = __fmaf_rn(m, v, ai);
     b.y = __fmaf_rn(-m, v, ai);
+  }
+  static __device__ __forceinline__ void run(float2 &a, float2 &b, const uint4 e) {
+    const float t = __uint_as_float(e.x);
+    const bool sine = e.w != 0u;
+    const float R = sine ? b.y : b.x;
+    const float S = sine ? b.x : b.y;
+    finish(a, b, e, __fmaf_rn(-t, S, R), __fmaf_rn(t, R, S));
+  }
+  // The path known at the call site (COS: cosine), for a twiddle that is
+  // the same in every lane: no operand selection.
+  template <bool COS>
+  static __device__ __forceinline__ void run_path(float2 &a, float2 &b, const uint4 e) {
+    const float t = __uint_as_float(e.x);
+    const float R = COS ? b.x : b.y;
+    const float S = COS ? b.y : b.x;
+    finish(a, b, e, __fmaf_rn(-t, S, R), __fmaf_rn(t, R, S));
   }
 };
 
@@ -182,17 +192,34 @@ template <int PREC, bool SCALED> struct BflyPacked {
       asm("{.reg .b32 n;\n\tneg.bf16x2 n, %1;\n\tfma.rn.bf16x2 %0, n, %2, %3;}" : "=r"(d) : "r"(a), "r"(b), "r"(c));
     return d;
   }
-  static __device__ __forceinline__ void run(uint32_t &a, uint32_t &b, const uint4 e) {
-    // X = cosine ? swap(b) : b ; Y = swap(X)
-    const uint32_t X = __byte_perm(b, b, e.z);
-    const uint32_t Y = swap_halves(X);
-    const uint32_t uv = fma2(e.x, X, Y);           // (u, v)
+  static __device__ __forceinline__ void finish(uint32_t &a, uint32_t &b, const uint4 e, uint32_t uv) {
     uint32_t ah = a;
     if (SCALED) ah = mul2(a, PREC == kFP16 ? 0x38003800u : 0x3F003F00u);  // x 0.5
     a = fma2(e.y, uv, ah);                         // (sigma m, m) (u, v) + a
     b = nfma2(e.y, uv, ah);                        // -(sigma m, m) (u, v) + a
   }
+  static __device__ __forceinline__ void run(uint32_t &a, uint32_t &b, const uint4 e) {
+    // X = cosine ? swap(b) : b ; Y = swap(X)
+    const uint32_t X = __byte_perm(b, b, e.z);
+    finish(a, b, e, fma2(e.x, X, swap_halves(X)));   // (u, v)
+  }
+  // The path known at the call site (COS: cosine), for a twiddle that is
+  // the same in every lane: X and Y are b and its swap in a fixed order, so
+  // no byte permute (the swap folds into the FMA's operand).
+  template <bool COS>
+  static __device__ __forceinline__ void run_path(uint32_t &a, uint32_t &b, const uint4 e) {
+    const uint32_t sb = swap_halves(b);
+    finish(a, b, e, COS ? fma2(e.x, sb, b) : fma2(e.x, b, sb));
+  }
 };
+
+// Cosine path of an unpacked entry (FP32: path word; FP16/BF16: the byte
+// permute selector, 0x1032 on the cosine path).
+template <int PREC>
+__device__ __forceinline__ bool tw_is_cosine(const uint4 e) {
+  if constexpr (PREC == kFP32) return e.w == 0u;
+  else return (e.z & 0xFFFFu) == 0x1032u;
+}
 
 template <bool SCALED> struct Bfly<kFP16, SCALED> : BflyPacked<kFP16, SCALED> {};
 template <bool SCALED> struct Bfly<kBF16, SCALED> : BflyPacked<kBF16, SCALED> {};

@@ -94,10 +94,27 @@ struct Fused {
     uint4 e;
     if constexpr (P == 0) e = tw0(((1 << I) - 1) + ql);
     else e = tw_load<PREC>(tw, ((1 << (P + I)) - 1) + j + (ql << P));
-    static_for<0, half>([&](auto qh_) {
-      constexpr int q = QTOP | decltype(qh_)::value;
-      Bfly<PREC, SCALED>::run(v[CI + q * C], v[CI + (q + half) * C], e);
-    });
+    if constexpr (PREC != kFP32 && P == 0 && half >= 4) {
+      // first stage: e is the same in every lane, so a uniform branch on
+      // its path runs the selection-free butterflies (packed precisions;
+      // measured slower for FP32, whose selection is two selects)
+      if (tw_is_cosine<PREC>(e)) {
+        static_for<0, half>([&](auto qh_) {
+          constexpr int q = QTOP | decltype(qh_)::value;
+          Bfly<PREC, SCALED>::template run_path<true>(v[CI + q * C], v[CI + (q + half) * C], e);
+        });
+      } else {
+        static_for<0, half>([&](auto qh_) {
+          constexpr int q = QTOP | decltype(qh_)::value;
+          Bfly<PREC, SCALED>::template run_path<false>(v[CI + q * C], v[CI + (q + half) * C], e);
+        });
+      }
+    } else {
+      static_for<0, half>([&](auto qh_) {
+        constexpr int q = QTOP | decltype(qh_)::value;
+        Bfly<PREC, SCALED>::run(v[CI + q * C], v[CI + (q + half) * C], e);
+      });
+    }
     if constexpr (I + 1 < RHO) {
       dfs<P, RHO, CI, I + 1, QTOP>(v, j, tw, tw0);
       dfs<P, RHO, CI, I + 1, QTOP + half>(v, j, tw, tw0);

@@ -39,10 +39,27 @@ struct GroupPasses {
     uint4 e;
     if constexpr (P0 == 0 && PL == 0) e = tw0(((1 << I) - 1) + ql);
     else e = tw_load<PREC>(twp, ((1 << p) - 1) + jg + (jloc << P0) + (ql << (PL + P0)));
-    static_for<0, half>([&](auto qh_) {
-      constexpr int q = QTOP | decltype(qh_)::value;
-      Bfly<PREC, SCALED>::run(v[CI + q * C], v[CI + (q + half) * C], e);
-    });
+    if constexpr (PREC != kFP32 && P0 == 0 && PL == 0 && half >= 4) {
+      // first stage: e is the same in every lane, so a uniform branch on
+      // its path runs the selection-free butterflies (packed precisions;
+      // measured slower for FP32, whose selection is two selects)
+      if (tw_is_cosine<PREC>(e)) {
+        static_for<0, half>([&](auto qh_) {
+          constexpr int q = QTOP | decltype(qh_)::value;
+          Bfly<PREC, SCALED>::template run_path<true>(v[CI + q * C], v[CI + (q + half) * C], e);
+        });
+      } else {
+        static_for<0, half>([&](auto qh_) {
+          constexpr int q = QTOP | decltype(qh_)::value;
+          Bfly<PREC, SCALED>::template run_path<false>(v[CI + q * C], v[CI + (q + half) * C], e);
+        });
+      }
+    } else {
+      static_for<0, half>([&](auto qh_) {
+        constexpr int q = QTOP | decltype(qh_)::value;
+        Bfly<PREC, SCALED>::run(v[CI + q * C], v[CI + (q + half) * C], e);
+      });
+    }
     if constexpr (I + 1 < RHO) {
       dfs<PL, RHO, CI, I + 1, QTOP>(v, jg, jloc, twp, tw0);
       dfs<PL, RHO, CI, I + 1, QTOP + half>(v, jg, jloc, twp, tw0);
