@@ -212,7 +212,7 @@ DSFFT_API fft_status fft_plan_get_table4(const fft_plan *plan, fft_direction dir
 
 /* Read and clear the plan's device error word.  Kernels whose waits are
  * bounded set it when such a wait gives up (about one second): the
- * FFT_VARIANT_FUSED_TMA kernel waiting for a bulk copy (bit 0), the 8-CTA
+ * FFT_VARIANT_FUSED_TMA kernel waiting for a bulk copy (bit 0), the
  * FP16/BF16 cluster kernel waiting for its phase-1 data (bit 1); the
  * affected blocks skip their remaining work, so the output is incomplete.
  * Returns FFT_ERR_TIMEOUT if it was set since the last call, else FFT_OK.

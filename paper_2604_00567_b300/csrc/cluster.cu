@@ -16,7 +16,7 @@
 // its last phase-1 exchange (split: each thread arrives once it has read,
 // computes its last phase-1 stage, and waits just before its remote
 // stores).  Then (B), every remote store has landed before phase 2 reads:
-// for 4-byte elements in 8-CTA clusters the stores are st.async and each
+// for 4-byte elements (FP16, BF16) the stores are st.async and each
 // CTA waits (bounded) on its own mbarrier until its phase-2 bytes have
 // arrived, with a relaxed cluster arrive after the stores and the matching
 // wait at exit so that no CTA leaves while another may still send to it;
@@ -74,9 +74,9 @@ struct Clus {
   static constexpr int SMEM = (GC1 * S1 > GC2 * S2 ? GC1 * S1 : GC2 * S2) * (int)sizeof(E);
   static constexpr int MINB = TPB >= 1024 ? 1 : 1024 / TPB;   // 1024 resident threads: <= 64 registers
   // Phase-1 outputs by st.async counted on the owner's mbarrier (measured
-  // faster on B300 for 4-byte elements in 8-CTA clusters), else by plain
-  // remote stores and a second cluster barrier.
-  static constexpr bool ASYNC = PREC != kFP32 && LOG2K == 3;
+  // faster on B300 for 4-byte elements), else by plain remote stores and a
+  // second cluster barrier (FP32: 8-byte st.async measured slower).
+  static constexpr bool ASYNC = PREC != kFP32;
   static_assert(GC2 * P2::T == TPB, "both phases use the same threads");
   static_assert(GC1 >= 32 && GC2 >= 32, "a warp must span 32 groups");
   static_assert(K <= 8, "portable cluster size");

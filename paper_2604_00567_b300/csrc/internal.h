@@ -120,7 +120,7 @@ int cluster_log2k(int prec, int log2n);
 cudaError_t prepare_cluster(int prec, int log2n);
 // `tw0`: the first per-pass entries (the fused kernel's stage-0 twiddles).
 // `status`: device word whose bit 1 a CTA sets when its bounded wait for
-// the phase-1 data gives up (the 8-CTA FP16/BF16 kernels); `tx_extra`
+// the phase-1 data gives up (the FP16/BF16 kernels); `tx_extra`
 // (fault injection, normally 0) is added to the bytes that wait expects.
 cudaError_t launch_cluster(int prec, int log2n, bool scaled, const void *in, void *out, const BatchItem *items,
                            int64_t batch, const uint4 *twp, const Stage0Twiddles &tw0, int *status,
