@@ -86,7 +86,9 @@ struct Fused {
   // arithmetic of the previous one.  tw0(i) returns per-pass entry i for the
   // first stage (the same for every thread): the constant bank or the global
   // table.
-  template <int P, int RHO, int CI, int I, int QTOP, class TW0>
+  // The butterflies run on columns [CB, CB + CN) of the thread's block
+  // (CN > 1 when those columns share j, hence every twiddle).
+  template <int P, int RHO, int CB, int CN, int I, int QTOP, class TW0>
   static __device__ __forceinline__ void dfs(E (&v)[R], int j, const uint4 *__restrict__ tw, const TW0 &tw0) {
     constexpr int C = R >> RHO;
     constexpr int half = 1 << (RHO - 1 - I);
@@ -94,51 +96,78 @@ struct Fused {
     uint4 e;
     if constexpr (P == 0) e = tw0(((1 << I) - 1) + ql);
     else e = tw_load<PREC>(tw, ((1 << (P + I)) - 1) + j + (ql << P));
-    if constexpr (PREC != kFP32 && P == 0 && half >= 4) {
+    if constexpr (PREC != kFP32 && P == 0 && half * CN >= 4) {
       // first stage: e is the same in every lane, so a uniform branch on
       // its path runs the selection-free butterflies (packed precisions;
       // measured slower for FP32, whose selection is two selects)
       if (tw_is_cosine<PREC>(e)) {
-        static_for<0, half>([&](auto qh_) {
-          constexpr int q = QTOP | decltype(qh_)::value;
-          Bfly<PREC, SCALED>::template run_path<true>(v[CI + q * C], v[CI + (q + half) * C], e);
+        static_for<0, CN>([&](auto c_) {
+          static_for<0, half>([&](auto qh_) {
+            constexpr int c = CB + decltype(c_)::value, q = QTOP | decltype(qh_)::value;
+            Bfly<PREC, SCALED>::template run_path<true>(v[c + q * C], v[c + (q + half) * C], e);
+          });
         });
       } else {
-        static_for<0, half>([&](auto qh_) {
-          constexpr int q = QTOP | decltype(qh_)::value;
-          Bfly<PREC, SCALED>::template run_path<false>(v[CI + q * C], v[CI + (q + half) * C], e);
+        static_for<0, CN>([&](auto c_) {
+          static_for<0, half>([&](auto qh_) {
+            constexpr int c = CB + decltype(c_)::value, q = QTOP | decltype(qh_)::value;
+            Bfly<PREC, SCALED>::template run_path<false>(v[c + q * C], v[c + (q + half) * C], e);
+          });
         });
       }
     } else {
-      static_for<0, half>([&](auto qh_) {
-        constexpr int q = QTOP | decltype(qh_)::value;
-        Bfly<PREC, SCALED>::run(v[CI + q * C], v[CI + (q + half) * C], e);
+      static_for<0, CN>([&](auto c_) {
+        static_for<0, half>([&](auto qh_) {
+          constexpr int c = CB + decltype(c_)::value, q = QTOP | decltype(qh_)::value;
+          Bfly<PREC, SCALED>::run(v[c + q * C], v[c + (q + half) * C], e);
+        });
       });
     }
     if constexpr (I + 1 < RHO) {
-      dfs<P, RHO, CI, I + 1, QTOP>(v, j, tw, tw0);
-      dfs<P, RHO, CI, I + 1, QTOP + half>(v, j, tw, tw0);
+      dfs<P, RHO, CB, CN, I + 1, QTOP>(v, j, tw, tw0);
+      dfs<P, RHO, CB, CN, I + 1, QTOP + half>(v, j, tw, tw0);
     }
   }
 
   template <int P, int RHO, class TW0>
   static __device__ __forceinline__ void compute(E (&v)[R], int tid, const uint4 *__restrict__ tw, const TW0 &tw0) {
     constexpr int C = R >> RHO;   // independent groups per thread
-    static_for<0, C>([&](auto c_) {
-      constexpr int c = decltype(c_)::value;
-      const int g = tid + c * T;
-      const int j = g & ((1 << P) - 1);
-      dfs<P, RHO, c, 0, 0>(v, j, tw, tw0);
-    });
+    if constexpr (C > 1 && T % (1 << P) == 0) {
+      // column c is group tid + c T, and 2^P divides T: every column has
+      // j = tid mod 2^P, so each twiddle is loaded once for all of them
+      dfs<P, RHO, 0, C, 0, 0>(v, tid & ((1 << P) - 1), tw, tw0);
+    } else {
+      static_for<0, C>([&](auto c_) {
+        constexpr int c = decltype(c_)::value;
+        const int g = tid + c * T;
+        const int j = g & ((1 << P) - 1);
+        dfs<P, RHO, c, 1, 0, 0>(v, j, tw, tw0);
+      });
+    }
   }
 
   // SIN: the first stage's values were read from `sm` (the bulk-copied
   // input), so its exchange must wait until every thread has read them.
+  // Stage schedule: stages of LOG2R passes, except that the remainder
+  // (LOG2N mod LOG2R passes) forms the second stage when there are three or
+  // more: it then starts at pass LOG2R, where 2^LOG2R divides T, so its
+  // columns share their twiddles (one load per twiddle instead of one per
+  // column; the last stages, with per-thread twiddles, are full).
+  static constexpr int REM = LOG2N % LOG2R;
+  static constexpr bool REM_SECOND = NSTAGES >= 3 && REM != 0;
+  static __host__ __device__ constexpr int stage_start(int s) {
+    return REM_SECOND && s >= 2 ? (s - 1) * LOG2R + REM : s * LOG2R;
+  }
+  static __host__ __device__ constexpr int stage_len(int s) {
+    return REM_SECOND ? (s == 1 ? REM : LOG2R)
+                      : ((LOG2N - s * LOG2R) < LOG2R ? (LOG2N - s * LOG2R) : LOG2R);
+  }
+
   template <int S, class TW0, bool SIN = false>
   static __device__ __forceinline__ void stages(E (&v)[R], E *sm, int tid, int lt, const uint4 *__restrict__ tw,
                                                 const TW0 &tw0, E *dst, bool active) {
-    constexpr int P = S * LOG2R;
-    constexpr int RHO = (LOG2N - P) < LOG2R ? (LOG2N - P) : LOG2R;
+    constexpr int P = stage_start(S);
+    constexpr int RHO = stage_len(S);
     constexpr int C = R >> RHO;
     if constexpr (S > 0) {
       // pad(tid + p T) = pad(tid) + p T + p T / 32 when 32 | T: one base
