@@ -65,8 +65,10 @@ struct Clus {
   static constexpr int M2 = 1 << LS2;
   static constexpr int GC1 = M2 / K;     // phase-1 groups per CTA
   static constexpr int GC2 = M1 / K;     // phase-2 groups per CTA
-  using P1 = GroupPasses<PREC, LS1, 0, SCALED>;
-  using P2 = GroupPasses<PREC, LS2, LS1, SCALED>;
+  // remainder stage first where measured faster: phase 2 always (its first
+  // stage then shares twiddles across columns), phase 1 for FP32 only
+  using P1 = GroupPasses<PREC, LS1, 0, SCALED, PREC == kFP32>;
+  using P2 = GroupPasses<PREC, LS2, LS1, SCALED, true>;
   static constexpr int R = P1::R;
   static constexpr int TPB = GC1 * P1::T;
   static constexpr int S1 = M1 + 1;      // padded group strides
@@ -81,8 +83,7 @@ struct Clus {
   static_assert(GC1 >= 32 && GC2 >= 32, "a warp must span 32 groups");
   static_assert(K <= 8, "portable cluster size");
   static_assert(LS1 > P1::LOG2R, "phase 1 has an exchange before its last stage");
-  static_assert(GC2 >= (1 << (((LS1 - 1) / P1::LOG2R) * P1::LOG2R)),
-                "a phase-1 output's owner depends only on its compile-time part");
+  static_assert(GC2 >= (1 << P1::LAST_PL), "a phase-1 output's owner depends only on its compile-time part");
 };
 
 // Asynchronous remote stores whose arrival the destination CTA counts on

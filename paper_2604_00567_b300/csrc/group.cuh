@@ -17,7 +17,7 @@
 
 namespace dsfft {
 
-template <int PREC, int LS, int P0, bool SCALED>
+template <int PREC, int LS, int P0, bool SCALED, bool REM_FIRST = true>
 struct GroupPasses {
   using E = typename Elem<PREC>::T;
   static constexpr int LOG2R = PREC == kFP32 ? 4 : 5;
@@ -25,11 +25,27 @@ struct GroupPasses {
   static constexpr int M = 1 << LS;
   static constexpr int T = M / R;
 
+  // Stage schedule: REM_FIRST puts the remainder (LS mod LOG2R passes)
+  // first, then stages of LOG2R passes: in the first stage every column of
+  // a thread has j_loc = 0, so its columns share each twiddle (one load for
+  // all of them), and the later stages hold one column each.  Otherwise
+  // stages of LOG2R passes with the remainder last.
+  static constexpr int REM = REM_FIRST ? LS % LOG2R : 0;
+  static __host__ __device__ constexpr int stage_start(int s) {
+    return s == 0 ? 0 : (REM ? REM : LOG2R) + (s - 1) * LOG2R;
+  }
+  static __host__ __device__ constexpr int stage_len(int s) {
+    return s == 0 && REM ? REM : ((LS - stage_start(s)) < LOG2R ? (LS - stage_start(s)) : LOG2R);
+  }
+  static constexpr int NSTAGES = (LS + LOG2R - 1) / LOG2R;
+  static constexpr int LAST_PL = stage_start(NSTAGES - 1);   // first local pass of the last stage
+
   // tw0(i): per-pass entry i for the first register stage when P0 = 0 (the
   // same for every thread: the constant bank).  Depth-first order over the
   // stage's passes (as in fused.cuh): pass I on a block of registers, then
-  // its two halves.
-  template <int PL, int RHO, int CI, int I, int QTOP, class TW0>
+  // its two halves, on columns [CB, CB + CN) (CN > 1 when those columns
+  // share j_loc, hence every twiddle).
+  template <int PL, int RHO, int CB, int CN, int I, int QTOP, class TW0>
   static __device__ __forceinline__ void dfs(E (&v)[R], int jg, int jloc, const uint4 *__restrict__ twp,
                                              const TW0 &tw0) {
     constexpr int C = R >> RHO;
@@ -39,30 +55,36 @@ struct GroupPasses {
     uint4 e;
     if constexpr (P0 == 0 && PL == 0) e = tw0(((1 << I) - 1) + ql);
     else e = tw_load<PREC>(twp, ((1 << p) - 1) + jg + (jloc << P0) + (ql << (PL + P0)));
-    if constexpr (PREC != kFP32 && P0 == 0 && PL == 0 && half >= 4) {
+    if constexpr (PREC != kFP32 && P0 == 0 && PL == 0 && half * CN >= 4) {
       // first stage: e is the same in every lane, so a uniform branch on
       // its path runs the selection-free butterflies (packed precisions;
       // measured slower for FP32, whose selection is two selects)
       if (tw_is_cosine<PREC>(e)) {
-        static_for<0, half>([&](auto qh_) {
-          constexpr int q = QTOP | decltype(qh_)::value;
-          Bfly<PREC, SCALED>::template run_path<true>(v[CI + q * C], v[CI + (q + half) * C], e);
+        static_for<0, CN>([&](auto c_) {
+          static_for<0, half>([&](auto qh_) {
+            constexpr int c = CB + decltype(c_)::value, q = QTOP | decltype(qh_)::value;
+            Bfly<PREC, SCALED>::template run_path<true>(v[c + q * C], v[c + (q + half) * C], e);
+          });
         });
       } else {
-        static_for<0, half>([&](auto qh_) {
-          constexpr int q = QTOP | decltype(qh_)::value;
-          Bfly<PREC, SCALED>::template run_path<false>(v[CI + q * C], v[CI + (q + half) * C], e);
+        static_for<0, CN>([&](auto c_) {
+          static_for<0, half>([&](auto qh_) {
+            constexpr int c = CB + decltype(c_)::value, q = QTOP | decltype(qh_)::value;
+            Bfly<PREC, SCALED>::template run_path<false>(v[c + q * C], v[c + (q + half) * C], e);
+          });
         });
       }
     } else {
-      static_for<0, half>([&](auto qh_) {
-        constexpr int q = QTOP | decltype(qh_)::value;
-        Bfly<PREC, SCALED>::run(v[CI + q * C], v[CI + (q + half) * C], e);
+      static_for<0, CN>([&](auto c_) {
+        static_for<0, half>([&](auto qh_) {
+          constexpr int c = CB + decltype(c_)::value, q = QTOP | decltype(qh_)::value;
+          Bfly<PREC, SCALED>::run(v[c + q * C], v[c + (q + half) * C], e);
+        });
       });
     }
     if constexpr (I + 1 < RHO) {
-      dfs<PL, RHO, CI, I + 1, QTOP>(v, jg, jloc, twp, tw0);
-      dfs<PL, RHO, CI, I + 1, QTOP + half>(v, jg, jloc, twp, tw0);
+      dfs<PL, RHO, CB, CN, I + 1, QTOP>(v, jg, jloc, twp, tw0);
+      dfs<PL, RHO, CB, CN, I + 1, QTOP + half>(v, jg, jloc, twp, tw0);
     }
   }
 
@@ -70,15 +92,21 @@ struct GroupPasses {
   static __device__ __forceinline__ void compute(E (&v)[R], int tid, int jg, const uint4 *__restrict__ twp,
                                                  const TW0 &tw0) {
     constexpr int C = R >> RHO;
-    static_for<0, C>([&](auto c_) {
-      constexpr int c = decltype(c_)::value;
-      // keep each group's twiddle loads next to their use: hoisting all
-      // C (2^RHO - 1) entries ahead would exhaust the registers
-      if constexpr (c > 0) asm volatile("" ::: "memory");
-      const int gl = tid + c * T;
-      const int jloc = gl & ((1 << PL) - 1);
-      dfs<PL, RHO, c, 0, 0>(v, jg, jloc, twp, tw0);
-    });
+    if constexpr (C > 1 && T % (1 << PL) == 0) {
+      // column c is local group tid + c T and 2^PL divides T: every column
+      // has j_loc = tid mod 2^PL, so each twiddle is loaded once for all
+      dfs<PL, RHO, 0, C, 0, 0>(v, jg, tid & ((1 << PL) - 1), twp, tw0);
+    } else {
+      static_for<0, C>([&](auto c_) {
+        constexpr int c = decltype(c_)::value;
+        // keep each group's twiddle loads next to their use: hoisting all
+        // C (2^RHO - 1) entries ahead would exhaust the registers
+        if constexpr (c > 0) asm volatile("" ::: "memory");
+        const int gl = tid + c * T;
+        const int jloc = gl & ((1 << PL) - 1);
+        dfs<PL, RHO, c, 1, 0, 0>(v, jg, jloc, twp, tw0);
+      });
+    }
   }
 
   // Runs all LS passes.  xw(idx, value) / xr(idx) write / read local
@@ -92,8 +120,8 @@ struct GroupPasses {
   static __device__ __forceinline__ void run(E (&v)[R], int tid, int jg, const uint4 *__restrict__ twp,
                                              const TW0 &tw0, XW &&xw, XR &&xr, SYNC &&sync, OUT &&out,
                                              FW &&first_write, PR &&post_read, PO &&pre_out) {
-    constexpr int PL = S * LOG2R;
-    constexpr int RHO = (LS - PL) < LOG2R ? (LS - PL) : LOG2R;
+    constexpr int PL = stage_start(S);
+    constexpr int RHO = stage_len(S);
     constexpr int C = R >> RHO;
     constexpr bool LAST = PL + RHO == LS;
     if constexpr (S > 0) {
