@@ -58,9 +58,13 @@ struct Sweep {
     S4 sgn;           // radix-4 plans: sign operand of the +-i d3 terms
   };
 
-  // levels of the register stage starting at local level PL
+  // levels of the register stage starting at local level PL: radix-2
+  // sweeps run the remainder (LS mod LOG2R levels) first, where every
+  // column of a thread has j_loc = 0 and so shares each twiddle, then
+  // stages of LOG2R levels
   static __host__ __device__ constexpr int stage_levels(int pl) {
-    return R4 ? r4_stage_levels(LS, LOG2R, pl) : ((LS - pl) < LOG2R ? (LS - pl) : LOG2R);
+    return R4 ? r4_stage_levels(LS, LOG2R, pl)
+              : (pl == 0 && LS % LOG2R != 0) ? LS % LOG2R : ((LS - pl) < LOG2R ? (LS - pl) : LOG2R);
   }
 
   // radix-4 passes of one stage: local levels [PL, PL + RHO), global
