@@ -104,7 +104,7 @@ int default_variant(int prec, int log2n) {
 // 26.2 % of HBM against 22.8 % for 9 + 9).
 int default_sweep_ls1(int prec, int log2n) {
   switch (log2n) {
-    case 17: return 8;
+    case 17: return prec == kFP32 ? 10 : 8;
     case 18: return prec == kFP32 ? 8 : 9;
     case 20: return prec == kFP32 ? 10 : 9;
     case 22: return prec == kFP32 ? 11 : 12;
