@@ -32,7 +32,16 @@
  * Errors: every call returns an fft_status.  Argument and plan errors are
  * returned synchronously and leave no work queued.  Launch failures return
  * FFT_ERR_CUDA (the CUDA error string is available from
- * fft_last_error_string on the calling thread).
+ * fft_last_error_string on the calling thread).  Device-side bounded waits
+ * that give up are reported through fft_plan_device_status.
+ *
+ * Fault injection for tests (environment, read when the call is made):
+ *   DSFFT_FAULT_ALLOC=k   the k-th device allocation of the library fails
+ *                         (FFT_ERR_OOM), counting from when the value is set;
+ *   DSFFT_FAULT_WAIT=1    plans created while it is set arm their kernels'
+ *                         bounded waits with 16 bytes that never arrive, so
+ *                         each such wait runs out (about one second) and the
+ *                         plan's device status word records it.
  */
 #ifndef DSFFT_H
 #define DSFFT_H
