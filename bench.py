@@ -343,10 +343,12 @@ def run_ours(args):
         pipes[l].close()
 
     c3 = batch_c3()
+    c4 = large_n_c4(hbm_peak)
 
-    serve = None
+    serve, serve_sweep = None, None
     if not args.no_serve:
         serve = serve_measure(args.serve_seconds)
+        serve_sweep = [serve_measure(0.5, rate=r, brief=True) for r in (10000.0, 40000.0, 80000.0)]
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -362,10 +364,13 @@ def run_ours(args):
                        "precision": PRECISION, "factorization": FACTORIZATION,
                        "input": "re/im i.i.d. uniform[-1,1], torch.Generator seeded",
                        "l2": "inputs 1 GiB per launch > 126 MB L2; no flush", "parallelism": f"replicas{world}"},
-            "roofline": roofline, "per_n": per_n, "fp32_plain": fp32, "radix4_fp16": radix4, "batch_c3": c3, "e2e": e2e,
+            "roofline": roofline, "per_n": per_n, "fp32_plain": fp32, "radix4_fp16": radix4, "batch_c3": c3,
+            "large_n_c4": c4, "e2e": e2e,
             "gpu_launches": K * sum(plans[l].info()["launches"] for l in log2ns),
-            "clocks": clocks, "cpu_baseline": cpu, "serve": serve,
+            "clocks": clocks, "cpu_baseline": cpu, "serve": serve, "serve_sweep": serve_sweep,
         }
+        # last key: a compact digest that survives a truncated log tail
+        line["summary"] = summary_text(per_n, fp32, c4, c3, serve, serve_sweep)
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -429,6 +434,69 @@ def batch_c3(steps: int = 10, count: int = 4096, seed: int = 1):
 
 
 # ---------------------------------------------------------------------------
+def large_n_c4(hbm_peak: float, steps: int = 5):
+    """Large transforms (grouped HBM sweeps): N = 2^20 and 2^24, batch 1 and
+    8, complex64 (FP32) and complex-FP16, forward; transforms/s and the
+    fraction of the HBM roofline (algorithmic bytes: one read and one write
+    of the batch), plus the forward + inverse round-trip error on the GPU."""
+    import torch
+    import paper_2604_00567_b300 as dsfft
+    from paper_2604_00567_b300 import signals
+    stream = torch.cuda.current_stream()
+    out = {}
+    for l in (20, 24):
+        n = 1 << l
+        for prec in ("fp32", "fp16"):
+            plan = dsfft.Plan(n, prec, FACTORIZATION)
+            eb = 8 if prec == "fp32" else 4
+            for batch in (1, 8):
+                x = signals.device_signal(batch, n, prec, seed=400 + l + batch)
+                y = torch.empty_like(x)
+                for _ in range(3):
+                    plan.exec(x, out=y)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                for _ in range(steps):
+                    plan.exec(x, out=y)
+                b.record(stream)
+                torch.cuda.synchronize()
+                ms = a.elapsed_time(b) / steps
+                nb = 2 * batch * n * eb
+                gbs = nb / (ms / 1e3) / 1e9
+                row = {"ms_per_exec": round(ms, 4), "transforms_per_s": batch / (ms / 1e3),
+                       "GB_per_s": round(gbs, 1), "frac_of_hbm": round(gbs / hbm_peak, 4),
+                       "sweep_passes": plan.info()["sweep_passes"]}
+                if batch == 1:
+                    z = plan.exec(y, direction=1)
+                    torch.cuda.synchronize()
+                    xs, zs = signals.from_torch(x, prec), signals.from_torch(z, prec)
+                    zs = zs if plan.scale_forward else zs / n
+                    row["round_trip_rel_l2"] = float(np.linalg.norm((zs - xs).ravel()) / np.linalg.norm(xs.ravel()))
+                out[f"{prec} 2^{l} x{batch}"] = row
+                del x, y
+            plan.close()
+    torch.cuda.empty_cache()
+    return out
+
+
+def summary_text(per_n, fp32, c4, c3, serve, serve_sweep) -> str:
+    """One short line with the per-size fractions of the HBM roofline."""
+    parts = ["fp16 " + " ".join(f"{k}:{100 * v['frac_of_hbm']:.1f}%" for k, v in per_n.items()),
+             "fp32 " + " ".join(f"{k}:{100 * v['frac_of_hbm']:.1f}%" for k, v in fp32.items())]
+    if c4:
+        parts.append("large " + " ".join(f"{k.replace(' ', '/')}:{100 * v['frac_of_hbm']:.1f}%" for k, v in c4.items()))
+    if c3:
+        parts.append(f"c3 {c3['ms_per_exec']}ms {c3['launches_per_exec']}launch "
+                     f"{c3['algorithmic_GB_per_s']}GB/s")
+    if serve:
+        parts.append(f"serve20k p50 {serve['p50_ms']} p99 {serve['p99_ms']}ms")
+    if serve_sweep:
+        parts.append("sweep " + " ".join(f"{int(r['rate'] / 1000)}k:p99 {r['p99_ms']}ms/{r['requests_per_s']:.0f}rps"
+                                          for r in serve_sweep))
+    return " | ".join(parts)
+
+
+# ---------------------------------------------------------------------------
 def serve_trace(seconds: float, rate: float, seed: int = 2):
     """Open-loop arrival trace: Poisson arrivals at ``rate`` req/s for
     ``seconds``; each request has U{1..256} signals of N = 2^e, e ~ U{8..18},
@@ -443,11 +511,11 @@ def serve_trace(seconds: float, rate: float, seed: int = 2):
 
 
 def serve_measure(seconds: float = 1.0, rate: float = 20000.0, budget: int = 40_000_000_000,
-                  max_tick_bytes: int = 1 << 30):
+                  max_tick_bytes: int = 1 << 30, brief: bool = False):
     """Serving loop under the arrival trace: inputs resident on the device
     (read from per-precision pools), outputs in the server's 40 GB arena
     (freed at completion).  Latency = completion seen by the scheduler -
-    submission, per request."""
+    submission, per request.  ``brief``: only the load-sweep fields."""
     import torch
     import paper_2604_00567_b300 as dsfft
     from paper_2604_00567_b300 import signals
@@ -483,6 +551,12 @@ def serve_measure(seconds: float = 1.0, rate: float = 20000.0, budget: int = 40_
     span = (t1 - t0) / 1e9
     transforms = int(sum(int(sig[c["tag"]]) for c in ok))
     payload = int(sum(2 * c["bytes"] for c in ok))
+    if brief:
+        return {"rate": rate, "seconds": seconds, "requests": len(arrivals), "completed_ok": len(ok),
+                "p50_ms": round(float(np.percentile(lat_ms, 50)), 3),
+                "p99_ms": round(float(np.percentile(lat_ms, 99)), 3),
+                "requests_per_s": len(ok) / span, "algorithmic_GB_per_s": round(payload / span / 1e9, 1),
+                "arena_peak_GB": round(st["arena_peak"] / 1e9, 3)}
     return {
         "config": "open-loop Poisson trace %.0f req/s for %.1f s (seed 2), U{1..256} signals, N = 2^U{8..18}, "
                   "FP32/FP16 p=0.5 (dual_select), inputs resident on the device, 40 GB arena, "
@@ -610,7 +684,8 @@ def run_reference(args):
     wall = time.perf_counter() - t0
     value = statistics.mean(v["value"] for v in vals)
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": "transforms/s", "n_gpus": 1,
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "transforms/s",
+        "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * wall / args.steps, 2),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f16",
         "data": "synthetic",
@@ -646,7 +721,8 @@ def run_exec_only(args):
 
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
-    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--gpus", type=int, default=1,
+                    help="replicas, one per GPU (started with torchrun when not already under it)")
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
@@ -678,6 +754,15 @@ def main():
     if args.serve_only:
         print(json.dumps({"serve": serve_measure(args.serve_seconds)}), flush=True)
         return
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        # one replica per GPU: start the ranks (torchrun) with the same arguments
+        cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={args.gpus}",
+               "--master-addr", "127.0.0.1", "--master-port", str(29500 + os.getpid() % 2000),
+               os.path.abspath(__file__)] + sys.argv[1:]
+        sys.exit(subprocess.call(cmd))
+    if world != args.gpus:
+        sys.exit(f"bench.py: --gpus {args.gpus} but WORLD_SIZE={world}")
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -308,14 +308,20 @@ DSFFT_API fft_status fft_batch_destroy(fft_batch *batch);
  * the library until exit) instead of memory the batch allocates.
  *   - `items`: `count` <= FFT_NOALLOC_MAX_ITEMS transforms, each with a plan
  *     created beforehand (fft_plan_create allocates; do that first), a
- *     direction and device input/output pointers (element-aligned; in == out
- *     is refused for plans on the HBM-sweep path).  More items:
- *     FFT_ERR_INVALID_SIZE.  All plans must be on one device.
- *   - Asynchronous on `stream`; the descriptors are copied from host memory
- *     before the call returns.
- *   - The first call on a device also looks up the device address of the
- *     array and sets the kernel's attributes; make that first call before
- *     any stream capture.
+ *     direction (FFT_FORWARD / FFT_INVERSE), `reserved` = 0 and device
+ *     input/output pointers aligned to the element size.  Refused: more
+ *     items (FFT_ERR_INVALID_SIZE); a bad direction, a nonzero reserved
+ *     field, a null or misaligned pointer, plans on different devices
+ *     (FFT_ERR_INVALID_ARG); in == out for a plan on the HBM-sweep path and
+ *     radix-4 plans (FFT_ERR_UNSUPPORTED).  A refused call launches nothing;
+ *     count = 0 returns FFT_OK without launching.
+ *   - Asynchronous on `stream`: the descriptors reach the device array as
+ *     the parameters of small copy kernels, so the call does not wait for
+ *     earlier work on `stream` and reads no host memory after it returns.
+ *   - The first call on a device (and the first after that device's context
+ *     is replaced, e.g. by cudaDeviceReset) also looks up the device address
+ *     of the array and sets the kernel's attributes; make that first call
+ *     before any stream capture.
  *   - Every call reuses the same array (the work counter is cleared at the
  *     start of each call); calls whose work overlaps on the GPU, e.g. on two
  *     streams, race on it — order them on one stream. */

@@ -11,12 +11,20 @@
 // library until the process exits.  The caller passes plans (created
 // beforehand) and the input/output buffers; nothing else is allocated.
 //
+// The descriptors reach the array as the parameters of small copy kernels
+// (the launch copies its parameters when it is issued), not by copies from
+// host memory: the call neither waits for the stream's earlier work (as a
+// copy from pageable memory would) nor leaves a copy that reads host memory
+// later, when the host array may already hold the next call's descriptors.
+//
 // The scratch array is shared by every call: its contents are those of the
 // last call (the work counter is cleared at the start of each call), and
 // calls whose work overlaps on the GPU (e.g. on two streams) race on it.
 // Host code reaches the array only through the address returned by
-// cudaGetSymbolAddress, looked up once per device with that device current,
-// on the first call made on that device.
+// cudaGetSymbolAddress, looked up with the device current on the first call
+// made on that device (and again if that device's context was replaced, e.g.
+// after cudaDeviceReset); device code in this file names it directly.
+#include <cuda.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -35,21 +43,44 @@ constexpr size_t kTilesOffset = kCounterBytes;
 constexpr size_t kItemsOffset = kTilesOffset + sizeof(BatchTile) * kMaxItems;
 constexpr size_t kScratchBytes = kItemsOffset + sizeof(BatchItem) * kMaxItems;
 constexpr int kMaxDevices = 64;
+static_assert(kTilesOffset % 16 == 0 && kItemsOffset % 16 == 0, "16-byte words");
+static_assert(sizeof(BatchTile) % 16 == 0 && sizeof(BatchItem) % 16 == 0, "16-byte words");
+
+// One copy launch: up to two runs of 16-byte words carried in the kernel's
+// parameters (32 KB parameter space, sm_70 and later with CUDA 12.1+).
+constexpr int kChunkWords = 2032;
+struct UploadChunk {
+  uint32_t offset[2];   // byte offsets of the two runs in the scratch array
+  uint32_t words[2];    // 16-byte words of each run (run 1 follows run 0 in data)
+  uint4 data[kChunkWords];
+};
+static_assert(sizeof(UploadChunk) <= 32764, "kernel parameter limit");
 
 }  // namespace
 
 // The batch's device-side scratch: [counter | tiles | items].
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
+__global__ void __launch_bounds__(256) noalloc_upload_kernel(const __grid_constant__ UploadChunk c) {
+  const uint32_t n0 = c.words[0], n = n0 + c.words[1];
+  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const uint32_t off = i < n0 ? c.offset[0] + 16u * i : c.offset[1] + 16u * (i - n0);
+    *reinterpret_cast<uint4 *>(g_noalloc_scratch + off) = c.data[i];
+  }
+}
+
 namespace {
 
-std::mutex g_mu;                          // guards everything below
+std::mutex g_mu;                            // guards everything below
 unsigned char *g_scratch_dev[kMaxDevices];  // device address of g_noalloc_scratch per device
-int g_grid[kMaxDevices];                  // persistent grid per device
+unsigned long long g_ctx_id[kMaxDevices];   // context the address belongs to
+int g_grid[kMaxDevices];                    // persistent grid per device
 
-// host staging (static: no heap allocation on this path)
+// host staging (static: no heap allocation on this path); the copy kernels
+// take their contents by value
 BatchTile g_tiles[kMaxItems];
 BatchItem g_items[kMaxItems];
+UploadChunk g_chunk;
 struct Key {
   PlanView view;
   const void *plan;
@@ -77,6 +108,71 @@ fft_status cuda_fail(cudaError_t e, const char *where) {
   snprintf(buf, sizeof buf, "%s: %s", where, cudaGetErrorString(e));
   set_last_error(buf);
   return FFT_ERR_CUDA;
+}
+
+// Unique id of the current context (the driver's cuCtxGetId, reached through
+// the runtime's entry-point query, so the library needs no link to libcuda).
+cudaError_t current_context_id(unsigned long long *id) {
+  using GetCurrent = CUresult (*)(CUcontext *);
+  using GetId = CUresult (*)(CUcontext, unsigned long long *);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  cudaError_t e;
+  if (!get_current || !get_id) {
+    cudaDriverEntryPointQueryResult q1, q2;
+    void *f1 = nullptr, *f2 = nullptr;
+    if ((e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1)) != cudaSuccess)
+      return e;
+    if ((e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2)) != cudaSuccess)
+      return e;
+    if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+      return cudaErrorSymbolNotFound;
+    get_current = reinterpret_cast<GetCurrent>(f1);
+    get_id = reinterpret_cast<GetId>(f2);
+  }
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return cudaErrorDeviceUninitialized;
+  if (get_id(ctx, id) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+  return cudaSuccess;
+}
+
+// Copies the runs (scratch offset, host source, bytes; multiples of 16) into
+// the scratch array by copy-kernel launches on `st`, packing consecutive runs
+// into each launch's parameters.
+struct Run {
+  size_t offset;
+  const void *src;
+  size_t bytes;
+};
+cudaError_t upload(const Run *runs, int nruns, cudaStream_t st) {
+  int seg = 0;
+  uint32_t used = 0;
+  auto flush = [&]() -> cudaError_t {
+    if (used == 0) return cudaSuccess;
+    if (seg < 2) g_chunk.words[1] = 0;
+    noalloc_upload_kernel<<<1, 256, 0, st>>>(g_chunk);
+    seg = 0;
+    used = 0;
+    return cudaGetLastError();
+  };
+  for (int r = 0; r < nruns; ++r) {
+    size_t done = 0;
+    const size_t words = runs[r].bytes / 16;
+    while (done < words) {
+      if (seg == 2 || used == (uint32_t)kChunkWords) {
+        const cudaError_t e = flush();
+        if (e != cudaSuccess) return e;
+      }
+      const size_t take = std::min<size_t>(words - done, (size_t)kChunkWords - used);
+      g_chunk.offset[seg] = (uint32_t)(runs[r].offset + 16 * done);
+      g_chunk.words[seg] = (uint32_t)take;
+      memcpy(&g_chunk.data[used], static_cast<const unsigned char *>(runs[r].src) + 16 * done, 16 * take);
+      used += (uint32_t)take;
+      done += take;
+      ++seg;
+    }
+  }
+  return flush();
 }
 
 }  // namespace
@@ -119,15 +215,19 @@ extern "C" fft_status fft_exec_batch_noalloc(const fft_noalloc_item *items, int6
     }
   } restore{prev, device};
 
-  // one-time set-up on this device: the device address of the scratch array
-  // (the array's name is only a host-side stand-in) and the launch grid
-  if (!g_scratch_dev[device]) {
+  // one-time set-up on this device (again if its context was replaced):
+  // the device address of the scratch array (the array's name is only a
+  // host-side stand-in) and the launch grid
+  unsigned long long ctx_id = 0;
+  if ((e = current_context_id(&ctx_id)) != cudaSuccess) return cuda_fail(e, "current context");
+  if (!g_scratch_dev[device] || g_ctx_id[device] != ctx_id) {
     void *p = nullptr;
     if ((e = cudaGetSymbolAddress(&p, g_noalloc_scratch)) != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress");
     int grid = 0;
     if ((e = prepare_batch_kernel(&grid)) != cudaSuccess) return cuda_fail(e, "batch kernel attributes");
     g_grid[device] = grid;
     g_scratch_dev[device] = static_cast<unsigned char *>(p);
+    g_ctx_id[device] = ctx_id;
   }
   unsigned char *base = g_scratch_dev[device];
   unsigned *d_counter = reinterpret_cast<unsigned *>(base);
@@ -164,14 +264,11 @@ extern "C" fft_status fft_exec_batch_noalloc(const fft_noalloc_item *items, int6
     i = j;
   }
   cudaStream_t st = (cudaStream_t)stream;
-  // pageable sources: each copy has read the host array when it returns
-  if ((e = cudaMemcpyAsync(d_items, g_items, sizeof(BatchItem) * (size_t)count, cudaMemcpyHostToDevice, st)) !=
-      cudaSuccess)
-    return cuda_fail(e, "copy items");
+  // descriptors into the scratch array by value (kernel parameters)
+  const Run runs[2] = {{kItemsOffset, g_items, sizeof(BatchItem) * (size_t)count},
+                       {kTilesOffset, g_tiles, sizeof(BatchTile) * (size_t)ntiles}};
+  if ((e = upload(runs, ntiles > 0 ? 2 : 1, st)) != cudaSuccess) return cuda_fail(e, "descriptor upload");
   if (ntiles > 0) {
-    if ((e = cudaMemcpyAsync(d_tiles, g_tiles, sizeof(BatchTile) * (size_t)ntiles, cudaMemcpyHostToDevice, st)) !=
-        cudaSuccess)
-      return cuda_fail(e, "copy tiles");
     // clears the work counter, then launches the persistent kernel
     if ((e = launch_batch_kernel(d_tiles, ntiles, d_items, d_counter, g_grid[device], st)) != cudaSuccess)
       return cuda_fail(e, "batch kernel launch");

@@ -30,6 +30,15 @@ def emulate(plan, x: np.ndarray, direction: int = -1) -> np.ndarray:
     return orc.emulate_fft(x, FMT[plan.precision], t, m, p, scaled=scaled, threads=8)
 
 
+def emulate_async(pool, plan, x: np.ndarray, direction: int = -1):
+    """:func:`emulate` on a thread pool: the plan's table is downloaded here
+    (on the calling thread), the emulation runs on ``pool`` (ctypes releases
+    the GIL, so several emulations run in parallel).  Returns a future."""
+    t, m, p = plan.table(direction)
+    scaled = plan.scale_forward if direction < 0 else plan.scale_inverse
+    return pool.submit(orc.emulate_fft, x, FMT[plan.precision], t, m, p, scaled, 1)
+
+
 def assert_bitexact(y: np.ndarray, ref: np.ndarray, what: str = ""):
     """Equal values, equal NaN positions and equal signs of zeros."""
     for part in ("real", "imag"):

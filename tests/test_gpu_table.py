@@ -91,3 +91,34 @@ def test_packed_words_consistent(dsfft):
     assert np.all(raw[:, 3] == (raw[:, 1] ^ 0x80008000))
     _, _, p = plan.table(-1)
     assert np.array_equal(p, sine.astype(np.int32))
+
+
+@pytest.mark.parametrize("fac", ["dual_select", "linzer_feig_clamped", "cosine"])
+@pytest.mark.parametrize("log2n", [10, 16, 20, 24])
+def test_rounded_entries_gpu_vs_host_counted(dsfft, fac, log2n, capsys):
+    """Counts (and prints) the rounded FP32/FP16/BF16 entries where the GPU
+    plan's table differs from the oracle's table built with the host's libm.
+    The two FP64 stages may differ by an ulp (CUDA's and glibc's cos/sin), and
+    the exact ties |w_r| = |w_i| at k = N/8 and 3N/8 may take different paths;
+    a rounded entry may differ only where its FP64 inputs differ."""
+    N = 1 << log2n
+    k = np.arange(N // 2)
+    tie = (k * 8 == N) | (k * 8 == 3 * N)
+    t64, m64, p64 = dsfft.twiddle_fp64(N, fac)
+    to64, mo64, po64 = orc.table(N, FAC[fac], orc.FP64)
+    fp64_differs = (t64 != to64) | (m64 != mo64) | (p64 != po64)
+    lines = []
+    for prec in ("fp32", "fp16", "bf16"):
+        plan = dsfft.Plan(N, prec, fac, scale_forward=False)
+        t, m, p = plan.table(-1)
+        to, mo, po = orc.table(N, FAC[fac], FMT[prec])
+        both_nan = np.isnan(t) & np.isnan(to)
+        differs = ((t != to) & ~both_nan) | (m != mo) | (p != po)
+        assert not np.any(differs & ~fp64_differs), "a rounded entry differs while its FP64 values agree"
+        assert not np.any((p != po) & ~tie), "paths differ away from the exact ties"
+        ties = ", ".join(f"k={int(i)}: path gpu {int(p[i])} host {int(po[i])}" for i in np.flatnonzero(tie))
+        lines.append(f"table-diff N=2^{log2n} {fac} {prec}: {int(differs.sum())} of {N // 2} rounded entries differ "
+                     f"(FP64 stage differs at {int(fp64_differs.sum())}; ties {ties or 'none'})")
+        plan.close()
+    with capsys.disabled():
+        print("\n" + "\n".join(lines))
