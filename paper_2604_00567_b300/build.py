@@ -24,13 +24,16 @@ CFLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcom
                  "-prec-div=true", "-prec-sqrt=true", "-I" + os.path.join(ROOT, "include")]
 
 
-def _deps():
-    return sorted(glob.glob(os.path.join(CSRC, "*")) + [os.path.join(ROOT, "include", "dsfft.h")])
+def _deps(src: str):
+    """A translation unit depends on itself, the headers next to it and the
+    public header (not on the other .cu files)."""
+    headers = glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h"))
+    return [src, os.path.join(ROOT, "include", "dsfft.h"), os.path.abspath(__file__)] + headers
 
 
 def _compile(src: str, verbose: bool) -> str:
     obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-    newest_dep = max(os.path.getmtime(d) for d in _deps())
+    newest_dep = max(os.path.getmtime(d) for d in _deps(src))
     if os.path.exists(obj) and os.path.getmtime(obj) >= newest_dep:
         return obj
     cmd = [NVCC, *CFLAGS, "-c", src, "-o", obj]

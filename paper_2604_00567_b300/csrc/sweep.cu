@@ -1,317 +1,22 @@
-// sweep.cu — FFT for N > 2^14 in two HBM sweeps of grouped radix-2 passes.
-//
-// Sweep 1 runs passes [0, LS1) and sweep 2 passes [LS1, m) of the m-pass
-// Stockham FFT (Section IV).  Before pass P0 the Stockham array is Z_P0; the
-// LS passes starting at P0 only mix, for each group g in [0, S) (S =
-// N/2^LS), the 2^LS values Z_P0[g + q S], q in [0, 2^LS), and write them to
-// Z_(P0+LS)[(g >> P0) 2^(P0+LS) + (g mod 2^P0) + o 2^P0], o in [0, 2^LS).
-// Inside a group the passes are the radix-2 butterflies of the whole
-// transform: local pass i at local index j_loc is global pass P0 + i at
-// j = (g mod 2^P0) + j_loc 2^P0, whose twiddle is per-pass entry
-// 2^(P0+i) - 1 + j.  So both sweeps apply exactly the butterflies of the
-// pass-by-pass algorithm and the result is bit-identical to it.
-//
-// A block holds G consecutive groups of one transform; lanes of a warp take
-// consecutive groups, so every global load (and the stores of sweep 2) are
-// runs of G consecutive elements.  Groups are exchanged between register
-// stages through shared memory laid out [element][group] (conflict-free).
-// Sweep 1's output of a block is one contiguous range of G 2^LS elements; it
-// is transposed through shared memory so that it is stored in order.
-#include "fused4.cuh"
+// sweep.cu — host dispatch of the two-sweep FFT for N > 2^14 (the kernels
+// are in sweep.cuh, instantiated per precision by sweep_fp32.cu,
+// sweep_fp16.cu and sweep_bf16.cu).
 #include "internal.h"
 
 namespace dsfft {
 
-__device__ __forceinline__ float2 sw_ldcs(const float2 *p) { return __ldcs(p); }
-__device__ __forceinline__ uint32_t sw_ldcs(const uint32_t *p) { return __ldcs(reinterpret_cast<const unsigned int *>(p)); }
-__device__ __forceinline__ void sw_stcs(float2 *p, float2 v) { __stcs(p, v); }
-__device__ __forceinline__ void sw_stcs(uint32_t *p, uint32_t v) { __stcs(reinterpret_cast<unsigned int *>(p), v); }
-
-// R4: radix-4 passes (the radix-4 extension, fused4.cuh): stages of whole
-// radix-4 passes with 16 points per thread; an odd LS (sweep 1 of an odd
-// log2 N) starts with the radix-2 pass of span 1.
-template <int PREC, int LS, bool SCALED, bool LAST, bool R4 = false>
-struct Sweep {
-  using E = typename Elem<PREC>::T;
-  static constexpr int EB = (int)sizeof(E);
-  static constexpr int LOG2R = (R4 || PREC == kFP32) ? 4 : 5;
-  static constexpr int R = 1 << LOG2R;
-  static constexpr int M = 1 << LS;                      // elements per group
-  static constexpr int T = M / R;                        // threads per group
-  // groups per block: at most 32, and at most 1024 threads (R points each)
-  static constexpr int LOG2G_CAP = (LOG2R == 4 ? 14 : 15) - LS;
-  static constexpr int LOG2G = LOG2G_CAP < 5 ? LOG2G_CAP : 5;
-  static constexpr int G = 1 << LOG2G;
-  static constexpr int TPB = G * T;
-  static_assert(TPB <= 1024, "one block holds at most 1024 threads");
-  static constexpr int SMEM_X = G * M * EB;              // exchange buffer
-  static constexpr int SMEM_T = LAST ? 0 : M * (G + 1) * EB;  // padded transpose buffer
-  static constexpr int SMEM = SMEM_X > SMEM_T ? SMEM_X : SMEM_T;
-  using S4 = typename std::conditional<PREC == kFP32, float, uint32_t>::type;
-
-  struct Ctx {
-    int tid, lg;
-    int64_t g;        // group index within the transform
-    int64_t jg;       // g mod 2^P0
-    int P0;
-    uint4 r2e;        // radix-4 plans: radix-2 entry k = 0 (W^0)
-    S4 sgn;           // radix-4 plans: sign operand of the +-i d3 terms
-  };
-
-  // levels of the register stage starting at local level PL: radix-2
-  // sweeps run the remainder (LS mod LOG2R levels) first, where every
-  // column of a thread has j_loc = 0 and so shares each twiddle, then
-  // stages of LOG2R levels
-  static __host__ __device__ constexpr int stage_levels(int pl) {
-    return R4 ? r4_stage_levels(LS, LOG2R, pl)
-              : (pl == 0 && LS % LOG2R != 0) ? LS % LOG2R : ((LS - pl) < LOG2R ? (LS - pl) : LOG2R);
-  }
-
-  // radix-4 passes of one stage: local levels [PL, PL + RHO), global
-  // P0 + PL + ...; per-pass radix-4 entries r4_offset(lvl) + (q - 1) L + j
-  template <int PL, int RHO>
-  static __device__ __forceinline__ void compute4(E (&v)[R], const Ctx &x, const uint4 *__restrict__ twp) {
-    constexpr int C = R >> RHO;
-    constexpr bool R2 = PL == 0 && (LS & 1);
-    constexpr int I0 = R2 ? 1 : 0;
-    static_assert((RHO - I0) % 2 == 0, "a stage holds whole radix-4 passes");
-    const int par = (x.P0 + LS) & 1;    // log2 N mod 2 (sweep 2 starts at an even or odd level)
-    static_for<0, C>([&](auto c_) {
-      constexpr int c = decltype(c_)::value;
-      if constexpr (c > 0) asm volatile("" ::: "memory");
-      const int gl = x.tid + c * T;
-      const int64_t jloc = gl & ((1 << PL) - 1);
-      if constexpr (R2) {
-        constexpr int half = 1 << (RHO - 1);
-        static_for<0, half>([&](auto qh_) {
-          constexpr int q = decltype(qh_)::value;
-          Bfly<PREC, SCALED>::run(v[c + q * C], v[c + (q + half) * C], x.r2e);
-        });
-      }
-      static_for<0, (RHO - I0) / 2>([&](auto k_) {
-        constexpr int i = I0 + 2 * decltype(k_)::value;
-        constexpr int Q = 1 << (RHO - i - 2);
-        const int lvl = x.P0 + PL + i;
-        const int64_t L = 1LL << lvl;
-        const int64_t tp = ((1LL << lvl) - 1 - par) + x.jg + (jloc << x.P0);
-        static_for<0, (1 << i)>([&](auto ql_) {
-          constexpr int ql = decltype(ql_)::value;
-          const int64_t at = tp + ((int64_t)ql << (PL + x.P0));
-          const uint4 e1 = tw_load<PREC>(twp, at);
-          const uint4 e2 = tw_load<PREC>(twp, at + L);
-          const uint4 e3 = tw_load<PREC>(twp, at + 2 * L);
-          constexpr int qtop = bitrev(ql, i) << (RHO - i);
-          static_for<0, Q>([&](auto qh_) {
-            constexpr int q0 = qtop | decltype(qh_)::value;
-            Bfly4<PREC, SCALED>::run(v[c + q0 * C], v[c + (q0 + Q) * C], v[c + (q0 + 2 * Q) * C],
-                                     v[c + (q0 + 3 * Q) * C], e1, e2, e3, x.sgn);
-          });
-        });
-      });
-    });
-  }
-
-  template <int PL, int RHO>
-  static __device__ __forceinline__ void compute(E (&v)[R], const Ctx &x, const uint4 *__restrict__ twp) {
-    constexpr int C = R >> RHO;
-    static_for<0, C>([&](auto c_) {
-      constexpr int c = decltype(c_)::value;
-      const int gl = x.tid + c * T;
-      const int64_t jloc = gl & ((1 << PL) - 1);
-      static_for<0, RHO>([&](auto i_) {
-        constexpr int i = decltype(i_)::value;
-        constexpr int half = 1 << (RHO - 1 - i);
-        const int p = x.P0 + PL + i;                       // global pass
-        const int64_t tp = ((1LL << p) - 1) + x.jg + (jloc << x.P0);
-        static_for<0, (1 << i)>([&](auto ql_) {
-          constexpr int ql = decltype(ql_)::value;
-          const uint4 e = tw_load<PREC>(twp, tp + ((int64_t)ql << (PL + x.P0)));
-          constexpr int qtop = bitrev(ql, i) << (RHO - i);
-          static_for<0, half>([&](auto qh_) {
-            constexpr int q = qtop | decltype(qh_)::value;
-            Bfly<PREC, SCALED>::run(v[c + q * C], v[c + (q + half) * C], e);
-          });
-        });
-      });
-    });
-  }
-
-  template <int PL>
-  static __device__ __forceinline__ void stages(E (&v)[R], E *sm, const Ctx &x, const uint4 *__restrict__ twp,
-                                                E *dst, int64_t stride, bool active) {
-    constexpr int RHO = stage_levels(PL);
-    constexpr int C = R >> RHO;
-    if constexpr (PL > 0) {
-      static_for<0, R>([&](auto p_) {
-        constexpr int p = decltype(p_)::value;
-        v[p] = sm[(x.tid + p * T) * G + x.lg];
-      });
-    }
-    if constexpr (R4) compute4<PL, RHO>(v, x, twp);
-    else compute<PL, RHO>(v, x, twp);
-    if constexpr (PL + RHO == LS) {
-      // local output o = tid + c T + bitrev(q) C T
-      if constexpr (LAST) {
-        if (active) {
-          static_for<0, C>([&](auto c_) {
-            constexpr int c = decltype(c_)::value;
-            static_for<0, (1 << RHO)>([&](auto q_) {
-              constexpr int q = decltype(q_)::value;
-              const int o = x.tid + c * T + (bitrev(q, RHO) << PL);
-              sw_stcs(dst + x.g + (int64_t)o * stride, v[c + q * C]);
-            });
-          });
-        }
-      } else {
-        if constexpr (PL > 0) __syncthreads();
-        static_for<0, C>([&](auto c_) {
-          constexpr int c = decltype(c_)::value;
-          static_for<0, (1 << RHO)>([&](auto q_) {
-            constexpr int q = decltype(q_)::value;
-            const int o = x.tid + c * T + (bitrev(q, RHO) << PL);
-            sm[o * (G + 1) + x.lg] = v[c + q * C];
-          });
-        });
-        __syncthreads();
-        // the block's output is the contiguous range [g0 2^LS, (g0 + G) 2^LS)
-        if (active) {
-          const int lin0 = threadIdx.x;
-#pragma unroll 4
-          for (int k = 0; k < G * M / TPB; ++k) {
-            const int lin = lin0 + k * TPB;
-            const int lg = lin >> LS, o = lin & (M - 1);
-            sw_stcs(dst + lin, sm[o * (G + 1) + lg]);
-          }
-        }
-      }
-    } else {
-      if constexpr (PL > 0) __syncthreads();
-      static_for<0, C>([&](auto c_) {
-        constexpr int c = decltype(c_)::value;
-        const int gl = x.tid + c * T;
-        const int base = ((gl >> PL) << (PL + RHO)) + (gl & ((1 << PL) - 1));
-        static_for<0, (1 << RHO)>([&](auto q_) {
-          constexpr int q = decltype(q_)::value;
-          sm[(base + (bitrev(q, RHO) << PL)) * G + x.lg] = v[c + q * C];
-        });
-      });
-      __syncthreads();
-      stages<PL + RHO>(v, sm, x, twp, dst, stride, active);
-    }
-  }
-};
-
-// Sweep 1 reads io.src and writes io.dst; sweep 2 (LAST) reads and writes
-// io.dst in place.
-template <int PREC, int LS, bool SCALED, bool LAST, class IO, bool R4 = false>
-__global__ void __launch_bounds__(Sweep<PREC, LS, SCALED, LAST, R4>::TPB)
-    sweep_fft_kernel(const IO io, int64_t batch, int log2n, int P0, const uint4 *__restrict__ twp,
-                     const uint4 r2e, const uint32_t sgn_bits) {
-  using K = Sweep<PREC, LS, SCALED, LAST, R4>;
-  using E = typename K::E;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  E *sm = reinterpret_cast<E *>(smem_raw);
-  const int64_t n = 1LL << log2n;
-  const int64_t S = n >> LS;                      // groups per transform = element stride
-  const int64_t blocks_per_tr = S >> K::LOG2G;
-  const int64_t tr = (int64_t)blockIdx.x / blocks_per_tr;
-  const int64_t g0 = ((int64_t)blockIdx.x - tr * blocks_per_tr) << K::LOG2G;
-  typename K::Ctx x;
-  x.lg = threadIdx.x & (K::G - 1);
-  x.tid = threadIdx.x >> K::LOG2G;
-  x.g = g0 + x.lg;
-  x.P0 = P0;
-  x.jg = x.g & ((1LL << P0) - 1);
-  x.r2e = r2e;
-  if constexpr (PREC == kFP32) x.sgn = __uint_as_float(sgn_bits);
-  else x.sgn = sgn_bits;
-  const bool active = tr < batch;
-  E v[K::R];
-  if (active) {
-    const E *src = (LAST ? io.dst(tr) : io.src(tr)) + x.g;
-    static_for<0, K::R>([&](auto p_) {
-      constexpr int p = decltype(p_)::value;
-      v[p] = sw_ldcs(src + (int64_t)(x.tid + p * K::T) * S);
-    });
-  } else {
-    static_for<0, K::R>([&](auto p_) { v[decltype(p_)::value] = E{}; });
-  }
-  // sweep 2 (LAST) writes group g's outputs at g + o S; sweep 1 writes the
-  // block's contiguous range starting at g0 2^LS
-  E *dst = !active ? nullptr : LAST ? io.dst(tr) : io.dst(tr) + (g0 << LS);
-  K::template stages<0>(v, sm, x, twp, dst, S, active);
-}
-
-// ---------------------------------------------------------------------------
-// dispatch: LS in [7, 12] (N = 2^15 .. 2^24 split as ceil(m/2) + floor(m/2))
-
-template <int PREC, int LS, bool SCALED, bool LAST, bool R4>
-static cudaError_t launch_sweep_one(const void *in, void *out, const BatchItem *items, int64_t batch, int log2n,
-                                    int P0, const uint4 *twp, const uint4 &r2e, uint32_t sgn, cudaStream_t stream) {
-  using K = Sweep<PREC, LS, SCALED, LAST, R4>;
-  using E = typename K::E;
-  const int64_t S = 1LL << (log2n - LS);
-  if (S < K::G) return cudaErrorInvalidValue;
-  const int64_t blocks = batch * (S >> K::LOG2G);
-  if (blocks > 0x7FFFFFFF) return cudaErrorInvalidConfiguration;
-  if (items) {
-    sweep_fft_kernel<PREC, LS, SCALED, LAST, GatherIO<E>, R4><<<(unsigned)blocks, K::TPB, K::SMEM, stream>>>(
-        GatherIO<E>{items}, batch, log2n, P0, twp, r2e, sgn);
-  } else {
-    sweep_fft_kernel<PREC, LS, SCALED, LAST, ContigIO<E>, R4><<<(unsigned)blocks, K::TPB, K::SMEM, stream>>>(
-        ContigIO<E>{static_cast<const E *>(in), static_cast<E *>(out), 1LL << log2n}, batch, log2n, P0, twp, r2e,
-        sgn);
-  }
-  return cudaGetLastError();
-}
-
-template <class F>
-static cudaError_t prepare_sweep_kernel(F kern, int smem) {
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-}
-
-template <int PREC, int LS, bool SCALED, bool LAST, bool R4>
-static cudaError_t prepare_sweep_one() {
-  using K = Sweep<PREC, LS, SCALED, LAST, R4>;
-  using E = typename K::E;
-  cudaError_t e = prepare_sweep_kernel(sweep_fft_kernel<PREC, LS, SCALED, LAST, ContigIO<E>, R4>, K::SMEM);
-  if (e != cudaSuccess) return e;
-  return prepare_sweep_kernel(sweep_fft_kernel<PREC, LS, SCALED, LAST, GatherIO<E>, R4>, K::SMEM);
-}
-
 using SweepFn = cudaError_t (*)(const void *, void *, const BatchItem *, int64_t, int, int, const uint4 *,
                                 const uint4 &, uint32_t, cudaStream_t);
-using SweepPrepFn = cudaError_t (*)();
-
-template <int PREC, bool SCALED, bool LAST, bool R4, int... LSs>
-struct SweepTable {
-  static constexpr SweepFn launch[] = {launch_sweep_one<PREC, LSs, SCALED, LAST, R4>...};
-  static constexpr SweepPrepFn prepare[] = {prepare_sweep_one<PREC, LSs, SCALED, LAST, R4>...};
-};
-
-#define DSFFT_LS_LIST 7, 8, 9, 10, 11, 12
-template <int PREC, bool R4>
-struct SweepSet {
-  using A = SweepTable<PREC, false, false, R4, DSFFT_LS_LIST>;
-  using B = SweepTable<PREC, true, false, R4, DSFFT_LS_LIST>;
-  using C = SweepTable<PREC, false, true, R4, DSFFT_LS_LIST>;
-  using D = SweepTable<PREC, true, true, R4, DSFFT_LS_LIST>;
-  static SweepFn get(bool scaled, bool last, int ls) {
-    const int i = ls - 7;
-    if (!last) return scaled ? B::launch[i] : A::launch[i];
-    return scaled ? D::launch[i] : C::launch[i];
-  }
-  static cudaError_t prepare(int ls) {
-    const int i = ls - 7;
-    for (SweepPrepFn f : {A::prepare[i], B::prepare[i], C::prepare[i], D::prepare[i]}) {
-      cudaError_t e = f();
-      if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
-  }
-};
+template <int PREC>
+SweepFn sweep_lookup(bool r4, bool scaled, bool last, int ls);
+template <int PREC>
+cudaError_t sweep_prepare_ls(bool r4, int ls);
+extern template SweepFn sweep_lookup<kFP32>(bool, bool, bool, int);
+extern template SweepFn sweep_lookup<kFP16>(bool, bool, bool, int);
+extern template SweepFn sweep_lookup<kBF16>(bool, bool, bool, int);
+extern template cudaError_t sweep_prepare_ls<kFP32>(bool, int);
+extern template cudaError_t sweep_prepare_ls<kFP16>(bool, int);
+extern template cudaError_t sweep_prepare_ls<kBF16>(bool, int);
 
 void sweep_split(int log2n, int *ls1, int *ls2) {
   *ls1 = (log2n + 1) / 2;
@@ -343,8 +48,8 @@ static cudaError_t prepare_sweeps_impl(int prec, int log2n, int ls1_req = 0) {
   }
   if (ls1 < 7 || ls1 > 12 || ls2 < 7 || ls2 > 12) return cudaErrorInvalidValue;
   for (int ls : {ls1, ls2}) {
-    cudaError_t e = prec == kFP32 ? SweepSet<kFP32, R4>::prepare(ls)
-                    : prec == kFP16 ? SweepSet<kFP16, R4>::prepare(ls) : SweepSet<kBF16, R4>::prepare(ls);
+    cudaError_t e = prec == kFP32 ? sweep_prepare_ls<kFP32>(R4, ls)
+                    : prec == kFP16 ? sweep_prepare_ls<kFP16>(R4, ls) : sweep_prepare_ls<kBF16>(R4, ls);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -363,8 +68,8 @@ static cudaError_t launch_sweeps_impl(int prec, int log2n, bool scaled, const vo
   }
   if (ls1 < 7 || ls1 > 12 || ls2 < 7 || ls2 > 12) return cudaErrorInvalidValue;
   auto get = [&](bool last, int ls) {
-    return prec == kFP32 ? SweepSet<kFP32, R4>::get(scaled, last, ls)
-           : prec == kFP16 ? SweepSet<kFP16, R4>::get(scaled, last, ls) : SweepSet<kBF16, R4>::get(scaled, last, ls);
+    return prec == kFP32 ? sweep_lookup<kFP32>(R4, scaled, last, ls)
+           : prec == kFP16 ? sweep_lookup<kFP16>(R4, scaled, last, ls) : sweep_lookup<kBF16>(R4, scaled, last, ls);
   };
   cudaError_t e = get(false, ls1)(in, out, items, batch, log2n, 0, twp, r2e, sgn, stream);
   if (e != cudaSuccess) return e;
