@@ -282,7 +282,13 @@ typedef struct fft_batch_info {
 DSFFT_API fft_status fft_batch_create(fft_batch **batch, const fft_batch_item *items, int64_t count,
                                       const fft_plan_opts *opts);
 
-/* Run every transform of the batch asynchronously on `stream`. */
+/* Run every transform of the batch asynchronously on `stream`.  The
+ * persistent launch runs on `stream`; the groups of larger transforms run on
+ * up to four streams the batch owns, forked from `stream` and joined back to
+ * it by events (so they overlap one another and the persistent launch's
+ * tail); work queued on `stream` after the call waits for all of them.  A
+ * batch must not run concurrently with itself (its work counter and internal
+ * streams are shared by its calls). */
 DSFFT_API fft_status fft_batch_exec(fft_batch *batch, void *stream);
 
 /* Same work as fft_batch_exec, through a CUDA graph: the first call captures

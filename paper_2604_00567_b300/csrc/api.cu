@@ -354,6 +354,13 @@ struct fft_batch {
     int64_t first, count;           // slice of d_items
   };
   std::vector<Large> large;
+  // internal streams for the large groups (forked from the caller's stream
+  // by `fork`, joined back by `join`), so that they overlap one another and
+  // the persistent kernel's tail; in a captured graph they are parallel
+  // branches
+  std::vector<cudaStream_t> side;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join;
   cudaStream_t capture_stream = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
@@ -362,23 +369,37 @@ struct fft_batch {
 
 namespace {
 
-// Queue every launch of the batch on `stream`.
+// Queue every launch of the batch: the persistent kernel on `stream`, the
+// large groups round-robin on the internal streams, forked from and joined
+// back to `stream` (work after the call on `stream` waits for all of it).
 cudaError_t batch_enqueue(const fft_batch *b, cudaStream_t stream) {
   cudaError_t e = cudaSuccess;
+  const size_t nside = b->side.size();
+  if (nside > 0) {
+    if ((e = cudaEventRecord(b->fork, stream)) != cudaSuccess) return e;
+    for (cudaStream_t s : b->side)
+      if ((e = cudaStreamWaitEvent(s, b->fork, 0)) != cudaSuccess) return e;
+  }
   if (b->ntiles > 0) {
     e = launch_batch_kernel(b->d_tiles, b->ntiles, b->d_items, b->d_counter, b->grid, stream);
     if (e != cudaSuccess) return e;
   }
-  for (const auto &g : b->large) {
+  for (size_t k = 0; k < b->large.size(); ++k) {
+    const auto &g = b->large[k];
     const fft_plan *p = g.plan;
     const bool scaled = p->scale[g.dir] != 0;
+    cudaStream_t st = nside > 0 ? b->side[k % nside] : stream;
     if (p->kernel == 2)
       e = launch_cluster(p->prec, p->log2n, scaled, nullptr, nullptr, b->d_items + g.first, g.count, p->twp[g.dir],
-                         p->tw0[g.dir], p->status, p->fault_tx, stream);
+                         p->tw0[g.dir], p->status, p->fault_tx, st);
     else
       e = launch_sweeps(p->prec, p->log2n, scaled, nullptr, nullptr, b->d_items + g.first, g.count, p->twp[g.dir],
-                        stream, p->sweep_ls1);
+                        st, p->sweep_ls1);
     if (e != cudaSuccess) return e;
+  }
+  for (size_t i = 0; i < nside; ++i) {
+    if ((e = cudaEventRecord(b->join[i], b->side[i])) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(stream, b->join[i], 0)) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
@@ -389,6 +410,9 @@ void batch_release(fft_batch *b) {
   if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+  for (cudaStream_t st : b->side) cudaStreamDestroy(st);
+  for (cudaEvent_t ev : b->join) cudaEventDestroy(ev);
+  if (b->fork) cudaEventDestroy(b->fork);
   if (b->d_items) cudaFree(b->d_items);
   if (b->d_tiles) cudaFree(b->d_tiles);
   if (b->d_counter) cudaFree(b->d_counter);
@@ -818,6 +842,20 @@ fft_status fft_batch_create(fft_batch **batch, const fft_batch_item *items, int6
       if ((e = device_alloc(&b->d_counter, sizeof(unsigned))) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc counter"); break; }
       if ((e = prepare_batch_kernel(&b->grid)) != cudaSuccess) { status = cuda_fail(e, "batch kernel attributes"); break; }
       b->device_bytes += (int64_t)(sizeof(BatchTile) * h_tiles.size() + sizeof(unsigned));
+    }
+    // up to four internal streams for the large groups
+    const size_t nside = std::min<size_t>(b->large.size(), 4);
+    if (nside > 0) {
+      if ((e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming)) != cudaSuccess) { status = cuda_fail(e, "event"); break; }
+      for (size_t i = 0; i < nside && e == cudaSuccess; ++i) {
+        cudaStream_t st = nullptr;
+        cudaEvent_t ev = nullptr;
+        if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) break;
+        b->side.push_back(st);
+        if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) break;
+        b->join.push_back(ev);
+      }
+      if (e != cudaSuccess) { status = cuda_fail(e, "internal streams"); break; }
     }
   } while (0);
   if (status != FFT_OK) {
