@@ -100,12 +100,12 @@ int default_variant(int prec, int log2n) {
 }
 
 // Built-in passes in sweep 1 for the sweeps variant (0: ceil(m/2)): the
-// split the autotuner measured fastest on a B300 (FP32 2^18: 8 + 10 passes
-// 26.2 % of HBM against 22.8 % for 9 + 9).
+// split measured fastest on a B300 (FP32 2^18: 10 + 8 passes 25.0 % of HBM
+// against 22.1 % for 8 + 10 and 21.4 % for 9 + 9).
 int default_sweep_ls1(int prec, int log2n) {
   switch (log2n) {
     case 17: return prec == kFP32 ? 10 : 8;
-    case 18: return prec == kFP32 ? 8 : 9;
+    case 18: return prec == kFP32 ? 10 : 9;
     case 20: return prec == kFP32 ? 10 : 9;
     case 22: return prec == kFP32 ? 11 : 12;
   }

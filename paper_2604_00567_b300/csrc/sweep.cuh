@@ -236,8 +236,8 @@ __global__ void __launch_bounds__(Sweep<PREC, LS, SCALED, LAST, R4>::TPB)
   x.lg = threadIdx.x & (K::G - 1);
   x.tid = threadIdx.x >> K::LOG2G;
   x.g = g0 + x.lg;
-  x.P0 = P0;
-  x.jg = x.g & ((1LL << P0) - 1);
+  x.P0 = LAST ? P0 : 0;   // sweep 1 always starts at pass 0: a constant the index arithmetic folds
+  x.jg = x.g & ((1LL << x.P0) - 1);
   x.r2e = r2e;
   if constexpr (PREC == kFP32) x.sgn = __uint_as_float(sgn_bits);
   else x.sgn = sgn_bits;

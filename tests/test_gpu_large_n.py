@@ -144,3 +144,46 @@ def test_every_sweep_length_bitexact(dsfft, prec, log2n, ls1):
             torch.cuda.synchronize()
             assert_bitexact(signals.from_torch(y, prec), futs[d].result(),
                             f"N=2^{log2n} {prec} sweeps {ls1} + {log2n - ls1} dir={d}")
+
+
+# the second sweep's interleaved form (several transforms of a batch per
+# block, lanes of different transforms sharing each twiddle): batches that
+# fill its transform slots and ragged ones that leave the last block part
+# empty, contiguous and gathered (fft_batch) pointers
+@pytest.mark.parametrize("prec,log2n,batch", [("fp16", 18, 5), ("fp16", 18, 8), ("fp16", 20, 3), ("fp32", 17, 6),
+                                              ("fp32", 18, 5), ("bf16", 19, 4), ("fp32", 20, 2)])
+def test_sweep2_interleaved_bitexact(dsfft, prec, log2n, batch):
+    import torch
+    N = 1 << log2n
+    plan = dsfft.Plan(N, prec, "dual_select")
+    assert plan.info()["kernel"] == 1
+    rows = [_row_signal(2700 + log2n, N, prec, b) for b in range(batch)]
+    xt = torch.cat([signals.to_torch(r, prec, "cuda") for r in rows], dim=0)
+    with ThreadPoolExecutor(max_workers=8) as pool:
+        futs = {d: [emulate_async(pool, plan, r, d) for r in rows] for d in (-1, 1)}
+        for d in (-1, 1):
+            y = plan.exec(xt, direction=d)
+            torch.cuda.synchronize()
+            for b in range(batch):
+                assert_bitexact(signals.from_torch(y[b:b + 1], prec), futs[d][b].result(),
+                                f"N=2^{log2n} {prec} batch {batch} transform {b} dir={d}")
+
+
+def test_sweep2_interleaved_gathered(dsfft):
+    """Six 2^18 FP16 transforms with their own buffers through fft_batch
+    (gathered pointers) against the oracle."""
+    import torch
+    N = 1 << 18
+    rows = [_row_signal(2800, N, "fp16", b) for b in range(6)]
+    ins = [signals.to_torch(r, "fp16", "cuda") for r in rows]
+    outs = [torch.empty_like(x) for x in ins]
+    batch = dsfft.Batch([(N, "fp16", "dual_select", -1, x, o) for x, o in zip(ins, outs)])
+    assert batch.info()["large_groups"] == 1
+    batch.exec()
+    torch.cuda.synchronize()
+    plan = dsfft.Plan(N, "fp16", "dual_select")
+    with ThreadPoolExecutor(max_workers=6) as pool:
+        futs = [emulate_async(pool, plan, r, -1) for r in rows]
+        for b in range(6):
+            assert_bitexact(signals.from_torch(outs[b], "fp16"), futs[b].result(), f"gathered transform {b}")
+    batch.close()
