@@ -6,8 +6,9 @@ complex-FP16, forward and inverse, each with the split of passes between
 the two sweeps that the plan runs by default (11 + 10, 11 + 11 / 12 + 10,
 12 + 11, 12 + 12); the first and last transform of batch-8 runs at 2^20
 and 2^24 in both formats; a forward + inverse round trip at 2^24 in both
-formats (Section V's round-trip check); and every sweep length LS = 7..12
-as the first and as the second sweep.
+formats (Section V's round-trip check); every sweep length LS = 7..12
+as the first and as the second sweep; and small batches (every transform)
+with contiguous and gathered pointers.
 
 The emulation of one 2^24-point transform takes tens of seconds of one
 host core, so the module computes every GPU output first and runs all the
@@ -146,13 +147,12 @@ def test_every_sweep_length_bitexact(dsfft, prec, log2n, ls1):
                             f"N=2^{log2n} {prec} sweeps {ls1} + {log2n - ls1} dir={d}")
 
 
-# the second sweep's interleaved form (several transforms of a batch per
-# block, lanes of different transforms sharing each twiddle): batches that
-# fill its transform slots and ragged ones that leave the last block part
-# empty, contiguous and gathered (fft_batch) pointers
+# small batches of the two-sweep path (odd counts, every transform checked;
+# the second sweep runs its blocks group-major across the batch), with
+# contiguous and with gathered (fft_batch) pointers
 @pytest.mark.parametrize("prec,log2n,batch", [("fp16", 18, 5), ("fp16", 18, 8), ("fp16", 20, 3), ("fp32", 17, 6),
                                               ("fp32", 18, 5), ("bf16", 19, 4), ("fp32", 20, 2)])
-def test_sweep2_interleaved_bitexact(dsfft, prec, log2n, batch):
+def test_sweep_small_batches_bitexact(dsfft, prec, log2n, batch):
     import torch
     N = 1 << log2n
     plan = dsfft.Plan(N, prec, "dual_select")
@@ -169,7 +169,7 @@ def test_sweep2_interleaved_bitexact(dsfft, prec, log2n, batch):
                                 f"N=2^{log2n} {prec} batch {batch} transform {b} dir={d}")
 
 
-def test_sweep2_interleaved_gathered(dsfft):
+def test_sweep_gathered_batch(dsfft):
     """Six 2^18 FP16 transforms with their own buffers through fft_batch
     (gathered pointers) against the oracle."""
     import torch
