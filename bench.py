@@ -511,7 +511,7 @@ def serve_trace(seconds: float, rate: float, seed: int = 2):
 
 
 def serve_measure(seconds: float = 1.0, rate: float = 20000.0, budget: int = 40_000_000_000,
-                  max_tick_bytes: int = 1 << 30, brief: bool = False):
+                  max_tick_bytes: int = 1 << 28, brief: bool = False, in_flight: int = 8):
     """Serving loop under the arrival trace: inputs resident on the device
     (read from per-precision pools), outputs in the server's 40 GB arena
     (freed at completion).  Latency = completion seen by the scheduler -
@@ -523,7 +523,8 @@ def serve_measure(seconds: float = 1.0, rate: float = 20000.0, budget: int = 40_
     pools = {"fp32": signals.device_signal(256, 1 << 18, "fp32", seed=21),
              "fp16": signals.device_signal(256, 1 << 18, "fp16", seed=22)}
     torch.cuda.synchronize()
-    srv = dsfft.Server(memory_budget=budget, release_on_complete=True, max_tick_bytes=max_tick_bytes)
+    srv = dsfft.Server(memory_budget=budget, release_on_complete=True, max_tick_bytes=max_tick_bytes,
+                       max_ticks_in_flight=in_flight)
     try:
         reqs = []
         for k in range(len(arrivals)):
@@ -560,8 +561,8 @@ def serve_measure(seconds: float = 1.0, rate: float = 20000.0, budget: int = 40_
     return {
         "config": "open-loop Poisson trace %.0f req/s for %.1f s (seed 2), U{1..256} signals, N = 2^U{8..18}, "
                   "FP32/FP16 p=0.5 (dual_select), inputs resident on the device, 40 GB arena, "
-                  "outputs freed at completion, ticks of at most %d MiB of output" % (rate, seconds,
-                                                                                max_tick_bytes >> 20),
+                  "outputs freed at completion, ticks of at most %d MiB of output, %d ticks in flight"
+                  % (rate, seconds, max_tick_bytes >> 20, in_flight),
         "requests": len(arrivals), "completed_ok": len(ok),
         "p50_ms": round(float(np.percentile(lat_ms, 50)), 3), "p99_ms": round(float(np.percentile(lat_ms, 99)), 3),
         "max_ms": round(float(lat_ms.max()), 3), "mean_ms": round(float(lat_ms.mean()), 3),
