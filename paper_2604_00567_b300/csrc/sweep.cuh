@@ -50,13 +50,39 @@ struct Sweep {
   static_assert(TPB <= 1024, "one block holds at most 1024 threads");
   static constexpr int SMEM_X = G * M * EB;              // exchange buffer
   static constexpr int SMEM_T = LAST ? 0 : M * (G + 1) * EB;  // padded transpose buffer
-  static constexpr int SMEM = SMEM_X > SMEM_T ? SMEM_X : SMEM_T;
+  // Twiddle staging (sweep 2, radix-2): in a middle register stage where
+  // the T threads of a group hold only 2^PL < T distinct j_loc (so T / 2^PL
+  // threads load each twiddle), the block loads the stage's G 2^PL
+  // (2^RHO - 1) entries once into shared memory after the exchange, and the
+  // butterflies read them there.  The first stage (its columns already share
+  // every twiddle, and a barrier there would hold up the arithmetic) and a
+  // stage whose twiddles are all distinct per thread (the last) read the
+  // table as before.
+  using TE = typename TwEntry<PREC>::T;
+  static __host__ __device__ constexpr bool staged(int pl, int rho) {
+    return LAST && !R4 && pl > 0 && (1 << pl) < T && rho >= 4;
+  }
+  static __host__ __device__ constexpr int tws_entries() {
+    int best = 0;
+    for (int pl = 0; pl < LS;) {
+      const int rho = stage_levels(pl);
+      const int cnt = staged(pl, rho) ? G * (1 << pl) * ((1 << rho) - 1) : 0;
+      best = cnt > best ? cnt : best;
+      pl += rho;
+    }
+    return best;
+  }
+  static constexpr int TWS = tws_entries();
+  static constexpr int SMEM_XT = SMEM_X + TWS * (int)sizeof(TE);
+  static constexpr int SMEM = SMEM_XT > SMEM_T ? SMEM_XT : SMEM_T;
   using S4 = typename std::conditional<PREC == kFP32, float, uint32_t>::type;
 
   struct Ctx {
     int tid, lg;
     int64_t g;        // group index within the transform
     int64_t jg;       // g mod 2^P0
+    int64_t g0;       // first group of the block
+    TE *tws;          // staged twiddles (after the exchange buffer)
     int P0;
     uint4 r2e;        // radix-4 plans: radix-2 entry k = 0 (W^0)
     S4 sgn;           // radix-4 plans: sign operand of the +-i d3 terms
@@ -115,6 +141,26 @@ struct Sweep {
     });
   }
 
+  // the staged twiddles of stage (PL, RHO): entry (i, ql, j_loc, lg) at
+  // ((2^i - 1 + ql) 2^PL + j_loc) G + lg
+  template <int PL, int RHO>
+  static __device__ __forceinline__ void load_tws(TE *tws, const Ctx &x, const uint4 *__restrict__ twp) {
+    constexpr int J = 1 << PL;
+    constexpr int CNT = G * J * ((1 << RHO) - 1);
+    const TE *tw = reinterpret_cast<const TE *>(twp);
+    for (int e = threadIdx.x; e < CNT; e += TPB) {
+      const int lg = e % G;
+      const int rest = e / G;
+      const int jloc = rest % J;
+      const int iq = rest / J;
+      const int i = 31 - __clz(iq + 1);
+      const int ql = iq + 1 - (1 << i);
+      const int64_t idx = ((1LL << (x.P0 + PL + i)) - 1) + (x.g0 + lg) + ((int64_t)jloc << x.P0) +
+                          ((int64_t)ql << (PL + x.P0));
+      tws[e] = __ldg(tw + idx);
+    }
+  }
+
   template <int PL, int RHO>
   static __device__ __forceinline__ void compute(E (&v)[R], const Ctx &x, const uint4 *__restrict__ twp) {
     constexpr int C = R >> RHO;
@@ -129,7 +175,11 @@ struct Sweep {
         const int64_t tp = ((1LL << p) - 1) + x.jg + (jloc << x.P0);
         static_for<0, (1 << i)>([&](auto ql_) {
           constexpr int ql = decltype(ql_)::value;
-          const uint4 e = tw_load<PREC>(twp, tp + ((int64_t)ql << (PL + x.P0)));
+          uint4 e;
+          if constexpr (staged(PL, RHO))
+            e = tw_unpack(x.tws[((((1 << i) - 1 + ql) << PL) + (int)jloc) * G + x.lg]);
+          else
+            e = tw_load<PREC>(twp, tp + ((int64_t)ql << (PL + x.P0)));
           constexpr int qtop = bitrev(ql, i) << (RHO - i);
           static_for<0, half>([&](auto qh_) {
             constexpr int q = qtop | decltype(qh_)::value;
@@ -152,7 +202,15 @@ struct Sweep {
       });
     }
     if constexpr (R4) compute4<PL, RHO>(v, x, twp);
-    else compute<PL, RHO>(v, x, twp);
+    else {
+      if constexpr (staged(PL, RHO)) {
+        // every thread is past the previous stage (the exchange barrier), so
+        // the buffer is free
+        load_tws<PL, RHO>(x.tws, x, twp);
+        __syncthreads();
+      }
+      compute<PL, RHO>(v, x, twp);
+    }
     if constexpr (PL + RHO == LS) {
       // local output o = tid + c T + bitrev(q) C T
       if constexpr (LAST) {
@@ -236,6 +294,8 @@ __global__ void __launch_bounds__(Sweep<PREC, LS, SCALED, LAST, R4>::TPB)
   x.lg = threadIdx.x & (K::G - 1);
   x.tid = threadIdx.x >> K::LOG2G;
   x.g = g0 + x.lg;
+  x.g0 = g0;
+  x.tws = reinterpret_cast<typename K::TE *>(smem_raw + K::SMEM_X);
   x.P0 = LAST ? P0 : 0;   // sweep 1 always starts at pass 0: a constant the index arithmetic folds
   x.jg = x.g & ((1LL << x.P0) - 1);
   x.r2e = r2e;
