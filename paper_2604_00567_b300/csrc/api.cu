@@ -101,12 +101,14 @@ int default_variant(int prec, int log2n) {
 
 // Built-in passes in sweep 1 for the sweeps variant (0: ceil(m/2)): the
 // split measured fastest on a B300 (FP32 2^18: 10 + 8 passes 25.0 % of HBM
-// against 22.1 % for 8 + 10 and 21.4 % for 9 + 9).
+// against 22.1 % for 8 + 10 and 21.4 % for 9 + 9; FP16 2^19: 9 + 10 23.0 %
+// against 22.0 % for 10 + 9).
 int default_sweep_ls1(int prec, int log2n) {
   switch (log2n) {
     case 17: return prec == kFP32 ? 10 : 8;
     case 18: return prec == kFP32 ? 10 : 9;
-    case 20: return prec == kFP32 ? 10 : 9;
+    case 19: return prec == kFP32 ? 11 : 9;
+    case 20: return 10;
     case 22: return prec == kFP32 ? 11 : 12;
   }
   return 0;
