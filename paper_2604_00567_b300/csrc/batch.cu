@@ -13,10 +13,11 @@
 namespace dsfft {
 
 constexpr int kBatchThreads = 1024;
-// shared memory of the largest tile: 1024 threads x 32 (FP16) or 16 (FP32)
-// points, one pad element per 32
-constexpr int kBatchSmem = kBatchThreads * 32 * 4 * 33 / 32;
-static_assert(kBatchSmem == kBatchThreads * 16 * 8 * 33 / 32, "FP32 tiles use the same space");
+// shared memory of the largest tile: 1024 threads x 16 eight-byte points
+// (FP32) with one pad element per 16; FP16/BF16 tiles (32 four-byte points,
+// one pad per 32) need less
+constexpr int kBatchSmem = kBatchThreads * 16 * 8 * 17 / 16;
+static_assert(kBatchSmem >= kBatchThreads * 32 * 4 * 33 / 32, "FP16 tiles fit");
 
 template <int PREC, int LOG2N, bool SCALED>
 __device__ __forceinline__ void batch_tile(const BatchTile &t, const BatchItem *items, unsigned char *smem) {

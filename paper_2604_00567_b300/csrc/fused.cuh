@@ -52,15 +52,19 @@ struct Fused {
   static constexpr int TPC = BTH / T;                    // transforms per block (tile)
   static constexpr int TPB = T * TPC;
   static constexpr int NSTAGES = (LOG2N + LOG2R - 1) / LOG2R;
-  static constexpr int PADN = N + (N >> 5);              // one pad element per 32 (conflict-free
-                                                         // exchanges for R = 32 (4-byte) / R = 16 (8-byte))
+  // One pad element per 32 four-byte (FP16/BF16) or per 16 eight-byte
+  // (FP32) elements: the exchanges are bank-conflict-free (a warp's 8-byte
+  // accesses are served 16 lanes per 128-byte wavefront, so 8-byte elements
+  // need the pad every 128 bytes).
+  static constexpr int PSH = sizeof(E) == 8 ? 4 : 5;
+  static constexpr int PADN = N + (N >> PSH);
   static constexpr int SMEM = NSTAGES > 1 ? TPC * PADN * (int)sizeof(E) : 0;
   // Blocks per SM the register allocation must allow: 1024 threads' worth
   // (at most 64 registers per thread), so at least half the SM's warps can
   // be resident.
   static constexpr int MINB = TPB >= 1024 ? 1 : 1024 / TPB;
 
-  static __device__ __forceinline__ int pad(int idx) { return idx + (idx >> 5); }
+  static __device__ __forceinline__ int pad(int idx) { return idx + (idx >> PSH); }
 
   // Exchange barrier of one transform's T threads: a warp barrier when they
   // share a warp, a named barrier per transform when a block holds several
@@ -170,12 +174,12 @@ struct Fused {
     constexpr int RHO = stage_len(S);
     constexpr int C = R >> RHO;
     if constexpr (S > 0) {
-      // pad(tid + p T) = pad(tid) + p T + p T / 32 when 32 | T: one base
-      // address plus compile-time offsets
+      // pad(tid + p T) = pad(tid) + p T + (p T >> PSH) when 2^PSH | T: one
+      // base address plus compile-time offsets
       const int pt = pad(tid);
       static_for<0, R>([&](auto p_) {
         constexpr int p = decltype(p_)::value;
-        if constexpr (T % 32 == 0) v[p] = sm[pt + p * T + ((p * T) >> 5)];
+        if constexpr (T % (1 << PSH) == 0) v[p] = sm[pt + p * T + ((p * T) >> PSH)];
         else v[p] = sm[pad(tid + p * T)];
       });
     }
@@ -192,9 +196,10 @@ struct Fused {
       }
     } else {
       if constexpr (S > 0 || SIN) sync(lt);   // previous exchange (or the input) fully read
-      // pad(base + off) = pad(base) + off + off / 32 when off is a multiple
-      // of 32 (P >= 5) or base is and off < 32 (P = 0, RHO = 5)
-      constexpr bool FOLD = P >= 5 || (P == 0 && RHO == 5);
+      // pad(base + off) = pad(base) + off + (off >> PSH) when off is a
+      // multiple of 2^PSH (P >= PSH) or base is and off < 2^RHO (P = 0,
+      // RHO >= PSH)
+      constexpr bool FOLD = P >= PSH || (P == 0 && RHO >= PSH);
       static_for<0, C>([&](auto c_) {
         constexpr int c = decltype(c_)::value;
         const int g = tid + c * T;
@@ -203,7 +208,7 @@ struct Fused {
         static_for<0, (1 << RHO)>([&](auto q_) {
           constexpr int q = decltype(q_)::value;
           constexpr int off = bitrev(q, RHO) << P;
-          if constexpr (FOLD) sm[pb + off + (off >> 5)] = v[c + q * C];
+          if constexpr (FOLD) sm[pb + off + (off >> PSH)] = v[c + q * C];
           else sm[pad(base + off)] = v[c + q * C];
         });
       });

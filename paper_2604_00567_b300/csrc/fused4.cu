@@ -77,7 +77,7 @@ FusedShape fused4_shape(int prec, int log2n) {
   const int tpc = bth / t;
   const int eb = prec == kFP32 ? 8 : 4;
   const int stages_gt1 = r4_stage_levels(log2n, r, 0) < log2n;
-  const int padn = (1 << log2n) + ((1 << log2n) >> 5);
+  const int padn = (1 << log2n) + ((1 << log2n) >> (eb == 8 ? 4 : 5));   // Fused::PADN
   return FusedShape{r, t, tpc, t * tpc, stages_gt1 ? tpc * padn * eb : 0};
 }
 

@@ -50,6 +50,7 @@ struct Fused4 : Fused<PREC, LOG2N, LOG2R, SCALED, BT> {
   using Base::R;
   using Base::T;
   using Base::pad;
+  using Base::PSH;
   using Base::sync;
   static constexpr int PAR = LOG2N & 1;
   using S = typename std::conditional<PREC == kFP32, float, uint32_t>::type;   // type of the sign operand
@@ -129,7 +130,7 @@ struct Fused4 : Fused<PREC, LOG2N, LOG2R, SCALED, BT> {
       const int pt = pad(tid);
       static_for<0, R>([&](auto p_) {
         constexpr int p = decltype(p_)::value;
-        if constexpr (T % 32 == 0) v[p] = sm[pt + p * T + ((p * T) >> 5)];
+        if constexpr (T % (1 << PSH) == 0) v[p] = sm[pt + p * T + ((p * T) >> PSH)];
         else v[p] = sm[pad(tid + p * T)];
       });
     }
@@ -146,7 +147,7 @@ struct Fused4 : Fused<PREC, LOG2N, LOG2R, SCALED, BT> {
       }
     } else {
       if constexpr (P > 0) sync(lt);
-      constexpr bool FOLD = P >= 5 || (P == 0 && RHO == 5);
+      constexpr bool FOLD = P >= PSH || (P == 0 && RHO >= PSH);
       static_for<0, C>([&](auto c_) {
         constexpr int c = decltype(c_)::value;
         const int g = tid + c * T;
@@ -155,7 +156,7 @@ struct Fused4 : Fused<PREC, LOG2N, LOG2R, SCALED, BT> {
         static_for<0, (1 << RHO)>([&](auto q_) {
           constexpr int q = decltype(q_)::value;
           constexpr int off = bitrev(q, RHO) << P;
-          if constexpr (FOLD) sm[pb + off + (off >> 5)] = v[c + q * C];
+          if constexpr (FOLD) sm[pb + off + (off >> PSH)] = v[c + q * C];
           else sm[pad(base + off)] = v[c + q * C];
         });
       });
