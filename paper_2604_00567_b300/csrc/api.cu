@@ -515,9 +515,10 @@ fft_status fft_plan_create(fft_plan **plan, int64_t n, fft_precision prec, fft_f
   if (const char *f = getenv("DSFFT_FAULT_WAIT")) p->fault_tx = atoi(f) > 0 ? 16u : 0u;
 
   const size_t entries = (size_t)(n / 2);
-  // per-pass tables hold the compact 8-byte entries for FP16/BF16
-  const int compact = (int)prec == kFP32 ? 0 : 1;
-  const size_t tw_bytes = compact ? sizeof(uint2) : sizeof(uint4);
+  // per-pass tables hold compact 8-byte entries (form 1 FP16/BF16, form 2
+  // FP32); the first-stage copies are 16-byte entries (form 0)
+  const int compact = (int)prec == kFP32 ? 2 : 1;
+  const size_t tw_bytes = sizeof(uint2);
   int *counts = nullptr;
   uint4 *head = nullptr;      // 16-byte forms of the first-stage entries: [dir][radix 2/4][31]
   cudaStream_t st = nullptr;
@@ -696,7 +697,7 @@ fft_status fft_plan_get_info(const fft_plan *plan, fft_plan_info *info) {
   info->points_per_thread = 1 << plan->shape.log2r;
   info->threads_per_transform = plan->shape.threads_per_transform;
   info->transforms_per_block = plan->shape.transforms_per_block;
-  const int64_t twb = plan->prec == kFP32 ? (int64_t)sizeof(uint4) : (int64_t)sizeof(uint2);
+  const int64_t twb = (int64_t)sizeof(uint2);   // compact per-pass entries
   info->table_bytes = (int64_t)2 * (plan->n / 2 * (int64_t)sizeof(uint4) + (plan->n - 1) * twb);
   if (plan->radix == 4) info->table_bytes += (int64_t)2 * (3 * plan->n / 4 * (int64_t)sizeof(uint4) + plan->n * twb);
   info->element_bytes = (int64_t)elem_bytes(plan->prec);

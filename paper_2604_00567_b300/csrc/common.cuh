@@ -76,31 +76,41 @@ struct GatherIO {
   __device__ __forceinline__ E *dst(int64_t k) const { return static_cast<E *>(items[k].out); }
 };
 
-// Per-pass twiddle entries as the kernels read them.  FP32: the 16-byte
-// packed entry above.  FP16/BF16: a compact 8-byte entry
-//   x = selector (low half) | t (high half),  y = (lo sigma*m, hi m)
-// from which tw_unpack rebuilds the 16-byte form with three integer
-// operations ((-t, t) by a sign flip and a byte permute, -(sigma m, m) by a
-// sign flip); the permute that uses the selector reads only its low 16 bits.
+// Per-pass twiddle entries as the kernels read them: compact 8-byte
+// entries, unpacked in registers to the 16-byte form above.
+//   FP16/BF16: x = selector (low half) | t (high half), y = (lo sigma*m,
+//              hi m); three integer operations rebuild (-t, t) (a sign flip
+//              and a byte permute) and -(sigma m, m) (a sign flip), and the
+//              permute that uses the selector reads only its low 16 bits.
+//   FP32     : x = t, y = m with the path in bit 30 (the top exponent bit,
+//              always 0 since |m| <= 1 for every factorization, halved or
+//              not); sigma m = m with the sign flipped on the sine path.
 // Half the bytes per entry halves the L1/L2 traffic of the later register
 // stages, whose lanes each read a different entry.
-template <int PREC> struct TwEntry { using T = uint4; };
-template <> struct TwEntry<kFP16> { using T = uint2; };
-template <> struct TwEntry<kBF16> { using T = uint2; };
+template <int PREC> struct TwEntry { using T = uint2; };
 
-__device__ __forceinline__ uint4 tw_unpack(const uint4 e) { return e; }
+template <int PREC>
 __device__ __forceinline__ uint4 tw_unpack(const uint2 e) {
   uint4 r;
-  r.x = __byte_perm(e.x, e.x ^ 0x80000000u, 0x3276);   // (lo -t, hi t)
-  r.y = e.y;
-  r.z = e.x;
-  r.w = e.y ^ 0x80008000u;
+  if constexpr (PREC == kFP32) {
+    const uint32_t path = (e.y >> 30) & 1u;
+    const uint32_t m = e.y & 0xBFFFFFFFu;
+    r.x = e.x;
+    r.y = m;
+    r.z = m ^ (path << 31);
+    r.w = path;
+  } else {
+    r.x = __byte_perm(e.x, e.x ^ 0x80000000u, 0x3276);   // (lo -t, hi t)
+    r.y = e.y;
+    r.z = e.x;
+    r.w = e.y ^ 0x80008000u;
+  }
   return r;
 }
 // Entry i of a per-pass table (the table's storage is TwEntry<PREC>::T[]).
 template <int PREC>
 __device__ __forceinline__ uint4 tw_load(const uint4 *table, int64_t i) {
-  return tw_unpack(__ldg(reinterpret_cast<const typename TwEntry<PREC>::T *>(table) + i));
+  return tw_unpack<PREC>(__ldg(reinterpret_cast<const typename TwEntry<PREC>::T *>(table) + i));
 }
 
 // Storage type of one complex element.

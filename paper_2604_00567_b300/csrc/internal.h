@@ -40,16 +40,18 @@ constexpr int kFusedMaxLog2N = 14;   // whole transform staged on chip
 // or 1/4).
 cudaError_t launch_build_table(int log2n, int64_t count, int fac, double eps, int prec, int inverse, double mscale,
                                uint4 *out, int *counts, cudaStream_t stream);
-// Per-pass table entries [0, count) of the N - 1; compact: the 8-byte
-// FP16/BF16 entries the kernels read (common.cuh TwEntry), else 16-byte.
-cudaError_t launch_per_pass_table(int log2n, const uint4 *table, void *twp, int64_t count, int compact,
+// Per-pass table entries [0, count) of the N - 1 in form `form` (table.cu
+// put_entry): 0 the 16-byte packed entry, 1 the compact 8-byte FP16/BF16
+// entry, 2 the compact 8-byte FP32 entry (the kernels read forms 1 and 2,
+// common.cuh TwEntry).
+cudaError_t launch_per_pass_table(int log2n, const uint4 *table, void *twp, int64_t count, int form,
                                   cudaStream_t stream);
 
 // Radix-4 passes (at levels par, par + 2, ..., par = log2 N mod 2; one
 // radix-2 pass at level 0 first when log2 N is odd): offset of level l in
 // the per-pass radix-4 table, which holds N - 1 - par entries in all.
 __host__ __device__ constexpr int64_t r4_offset(int l, int par) { return (int64_t(1) << l) - 1 - par; }
-cudaError_t launch_per_pass_table4(int log2n, const uint4 *table4, void *twp4, int64_t count, int compact,
+cudaError_t launch_per_pass_table4(int log2n, const uint4 *table4, void *twp4, int64_t count, int form,
                                    cudaStream_t stream);
 cudaError_t launch_fp64_table(int log2n, int fac, double eps, double *t, double *m, int *path,
                               cudaStream_t stream);

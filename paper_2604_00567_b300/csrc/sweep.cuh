@@ -177,7 +177,7 @@ struct Sweep {
           constexpr int ql = decltype(ql_)::value;
           uint4 e;
           if constexpr (staged(PL, RHO))
-            e = tw_unpack(x.tws[((((1 << i) - 1 + ql) << PL) + (int)jloc) * G + x.lg]);
+            e = tw_unpack<PREC>(x.tws[((((1 << i) - 1 + ql) << PL) + (int)jloc) * G + x.lg]);
           else
             e = tw_load<PREC>(twp, tp + ((int64_t)ql << (PL + x.P0)));
           constexpr int qtop = bitrev(ql, i) << (RHO - i);

@@ -87,11 +87,15 @@ __global__ void build_table_kernel(int log2n, int64_t count, int fac, double eps
   if (counts) atomicAdd(&counts[e.sine], 1);
 }
 
-// Store per-pass entry i: the 16-byte packed entry, or (compact) its 8-byte
-// form {selector | t << 16, (sigma m, m)} (common.cuh TwEntry).
-__device__ __forceinline__ void put_entry(void *out, int64_t i, const uint4 w, int compact) {
-  if (compact)
+// Store per-pass entry i: the 16-byte packed entry (form 0), or its
+// compact 8-byte form (common.cuh TwEntry): form 1 for FP16/BF16
+// {selector | t << 16, (sigma m, m)}, form 2 for FP32 {t, m | path << 30}
+// (|m| <= 1, so bit 30 of m is free).
+__device__ __forceinline__ void put_entry(void *out, int64_t i, const uint4 w, int form) {
+  if (form == 1)
     static_cast<uint2 *>(out)[i] = make_uint2((w.z & 0xFFFFu) | (w.x & 0xFFFF0000u), w.y);
+  else if (form == 2)
+    static_cast<uint2 *>(out)[i] = make_uint2(w.x, w.y | (w.w << 30));
   else
     static_cast<uint4 *>(out)[i] = w;
 }
@@ -100,20 +104,20 @@ __device__ __forceinline__ void put_entry(void *out, int64_t i, const uint4 w, i
 // table[j N/2^(p+1)] for j in [0, 2^p); it is stored at twp[2^p - 1 + j]
 // (entries [0, count) of the N - 1).
 __global__ void per_pass_table_kernel(int log2n, const uint4 *__restrict__ table, void *__restrict__ twp,
-                                      int64_t count, int compact) {
+                                      int64_t count, int form) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= count) return;
   int p = 63 - __clzll(i + 1);            // 2^p - 1 <= i < 2^(p+1) - 1
   const int64_t j = i - ((1LL << p) - 1);
-  put_entry(twp, i, table[j << (log2n - p - 1)], compact);
+  put_entry(twp, i, table[j << (log2n - p - 1)], form);
 }
 
-cudaError_t launch_per_pass_table(int log2n, const uint4 *table, void *twp, int64_t count, int compact,
+cudaError_t launch_per_pass_table(int log2n, const uint4 *table, void *twp, int64_t count, int form,
                                   cudaStream_t stream) {
   if (count <= 0) return cudaSuccess;
   const int threads = 256;
   const unsigned blocks = (unsigned)((count + threads - 1) / threads);
-  per_pass_table_kernel<<<blocks, threads, 0, stream>>>(log2n, table, twp, count, compact);
+  per_pass_table_kernel<<<blocks, threads, 0, stream>>>(log2n, table, twp, count, form);
   return cudaGetLastError();
 }
 
@@ -141,7 +145,7 @@ cudaError_t launch_build_table(int log2n, int64_t count, int fac, double eps, in
 // [r4_offset(l), r4_offset(l) + 3L) as three runs of L entries, run q - 1
 // holding W_4L^(q j) = table4[q j N/(4L)] for j in [0, L), q = 1, 2, 3.
 __global__ void per_pass_table4_kernel(int log2n, const uint4 *__restrict__ table4, void *__restrict__ twp4,
-                                       int64_t count, int compact) {
+                                       int64_t count, int form) {
   const int par = log2n & 1;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= count) return;
@@ -150,15 +154,15 @@ __global__ void per_pass_table4_kernel(int log2n, const uint4 *__restrict__ tabl
   const int64_t L = 1LL << l;
   const int64_t rem = i - r4_offset(l, par);
   const int64_t q = rem / L + 1, j = rem % L;
-  put_entry(twp4, i, table4[(q * j) << (log2n - l - 2)], compact);
+  put_entry(twp4, i, table4[(q * j) << (log2n - l - 2)], form);
 }
 
-cudaError_t launch_per_pass_table4(int log2n, const uint4 *table4, void *twp4, int64_t count, int compact,
+cudaError_t launch_per_pass_table4(int log2n, const uint4 *table4, void *twp4, int64_t count, int form,
                                    cudaStream_t stream) {
   if (count <= 0) return cudaSuccess;
   const int threads = 256;
   const unsigned blocks = (unsigned)((count + threads - 1) / threads);
-  per_pass_table4_kernel<<<blocks, threads, 0, stream>>>(log2n, table4, twp4, count, compact);
+  per_pass_table4_kernel<<<blocks, threads, 0, stream>>>(log2n, table4, twp4, count, form);
   return cudaGetLastError();
 }
 
