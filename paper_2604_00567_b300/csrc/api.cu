@@ -100,15 +100,16 @@ int default_variant(int prec, int log2n) {
 }
 
 // Built-in passes in sweep 1 for the sweeps variant (0: ceil(m/2)): the
-// split measured fastest on a B300 (FP32 2^18: 10 + 8 passes 25.0 % of HBM
-// against 22.1 % for 8 + 10 and 21.4 % for 9 + 9; FP16 2^19: 9 + 10 23.0 %
-// against 22.0 % for 10 + 9).
+// split measured fastest on a B300 (256 MiB batches; FP32 2^18: 10 + 8
+// passes 30.3 % of HBM against 28.6 % for 8 + 10 and 24.8 % for 9 + 9;
+// FP16 2^20: 11 + 9 21.9 % against 20.9 % for 10 + 10).
 int default_sweep_ls1(int prec, int log2n) {
   switch (log2n) {
     case 17: return prec == kFP32 ? 10 : 8;
     case 18: return prec == kFP32 ? 10 : 9;
     case 19: return prec == kFP32 ? 11 : 9;
-    case 20: return 10;
+    case 20: return prec == kFP32 ? 12 : 11;
+    case 21: return prec == kFP32 ? 10 : 12;
     case 22: return prec == kFP32 ? 11 : 12;
   }
   return 0;
@@ -195,8 +196,9 @@ void cache_write(const char *path, const std::map<std::string, int> &m) {
 // Time every valid variant of plan p on a 128 MiB batch and keep the
 // fastest (forward direction).
 // Candidate (variant, passes in sweep 1) of the autotuner: every variant
-// the size has, the sweeps with each valid split within one pass of the
-// balanced one.  Cached as variant * 100 + passes (0: the default split).
+// the size has, the sweeps with each valid split within two passes of the
+// balanced one (the measured best splits of a B300 lie there, e.g. FP32
+// 2^20: 12 + 8).  Cached as variant * 100 + passes (0: the default split).
 struct Candidate {
   int variant, ls1;
 };
@@ -207,7 +209,7 @@ cudaError_t apply_candidate(fft_plan *p, const Candidate &c) {
 }
 
 cudaError_t autotune_plan(fft_plan *p) {
-  Candidate cands[8];
+  Candidate cands[16];
   int nc = 0;
   for (int v = FFT_VARIANT_FUSED_WIDE; v <= FFT_VARIANT_FUSED_TMA; ++v) {
     if (!variant_valid(p->prec, p->log2n, v)) continue;
@@ -216,8 +218,8 @@ cudaError_t autotune_plan(fft_plan *p) {
       continue;
     }
     const int mid = (p->log2n + 1) / 2;
-    for (int l = mid - 1; l <= mid + 1; ++l)
-      if (sweep_ls1_valid(p->log2n, l)) cands[nc++] = Candidate{v, l == mid ? 0 : l};
+    for (int l = mid - 2; l <= mid + 2; ++l)
+      if (sweep_ls1_valid(p->log2n, l)) cands[nc++] = Candidate{v, l};
   }
   if (nc < 2) return cudaSuccess;
   cudaDeviceProp prop;

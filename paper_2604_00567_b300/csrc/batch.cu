@@ -74,8 +74,9 @@ int batch_tile_capacity(int prec, int log2n) {
 cudaError_t prepare_batch_kernel(int *grid) {
   cudaError_t e = cudaFuncSetAttribute(batch_fft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchSmem);
   if (e != cudaSuccess) return e;
+  // one block per SM: the rest of the L1/shared array stays L1
   e = cudaFuncSetAttribute(batch_fft_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
-                           cudaSharedmemCarveoutMaxShared);
+                           carveout_for(kBatchSmem, 1));
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per_sm = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;

@@ -261,11 +261,16 @@ static cudaError_t launch_cluster_one(const void *in, void *out, const BatchItem
   return cudaGetLastError();
 }
 
+// Carveout: the shared memory of the CTAs the register budget lets reside
+// (MINB); the rest of the SM's L1/shared array stays L1 for the phase-2
+// twiddles (measured on B300, FP16 N = 2^16: 41.1 % of HBM against 37.7 %
+// with the maximum carveout; one CTA fewer per SM for a larger L1: 34.3 %).
 template <class F>
-static cudaError_t prepare_cluster_kernel(F kern, int smem) {
+static cudaError_t prepare_cluster_kernel(F kern, int smem, int nblk) {
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  return cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                              carveout_for(smem, nblk));
 }
 
 template <int PREC, int LOG2N, int LOG2K>
@@ -273,10 +278,10 @@ static cudaError_t prepare_cluster_one() {
   using K = Clus<PREC, LOG2N, LOG2K, false>;
   using E = typename K::E;
   cudaError_t e;
-  if ((e = prepare_cluster_kernel(cluster_fft_kernel<PREC, LOG2N, LOG2K, false, ContigIO<E>>, K::SMEM)) != cudaSuccess) return e;
-  if ((e = prepare_cluster_kernel(cluster_fft_kernel<PREC, LOG2N, LOG2K, true, ContigIO<E>>, K::SMEM)) != cudaSuccess) return e;
-  if ((e = prepare_cluster_kernel(cluster_fft_kernel<PREC, LOG2N, LOG2K, false, GatherIO<E>>, K::SMEM)) != cudaSuccess) return e;
-  return prepare_cluster_kernel(cluster_fft_kernel<PREC, LOG2N, LOG2K, true, GatherIO<E>>, K::SMEM);
+  if ((e = prepare_cluster_kernel(cluster_fft_kernel<PREC, LOG2N, LOG2K, false, ContigIO<E>>, K::SMEM, K::MINB)) != cudaSuccess) return e;
+  if ((e = prepare_cluster_kernel(cluster_fft_kernel<PREC, LOG2N, LOG2K, true, ContigIO<E>>, K::SMEM, K::MINB)) != cudaSuccess) return e;
+  if ((e = prepare_cluster_kernel(cluster_fft_kernel<PREC, LOG2N, LOG2K, false, GatherIO<E>>, K::SMEM, K::MINB)) != cudaSuccess) return e;
+  return prepare_cluster_kernel(cluster_fft_kernel<PREC, LOG2N, LOG2K, true, GatherIO<E>>, K::SMEM, K::MINB);
 }
 
 cudaError_t prepare_cluster(int prec, int log2n) {

@@ -43,9 +43,7 @@ static cudaError_t prepare_one() {
   using K = Fused<PREC, LOG2N, LOG2R, false>;
   // Shared-memory carveout: enough for the blocks the register budget lets
   // reside (MINB, at least one), the rest stays L1 for the twiddle table.
-  const int per_block = K::SMEM + 1024;
-  int carve = (int)((100LL * per_block * (K::MINB > 0 ? K::MINB : 1) + 228 * 1024 - 1) / (228 * 1024));
-  carve = carve < 1 ? 1 : carve > 100 ? 100 : carve;
+  const int carve = carveout_for(K::SMEM, K::MINB);
   for (auto kern : {fused_fft_kernel<PREC, LOG2N, LOG2R, false>, fused_fft_kernel<PREC, LOG2N, LOG2R, true>}) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, carve);
     if (e != cudaSuccess) return e;

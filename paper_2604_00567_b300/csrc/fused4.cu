@@ -40,9 +40,7 @@ template <int PREC, int LOG2N>
 static cudaError_t prepare4_one() {
   constexpr int LOG2R = r4_log2r(LOG2N);
   using K = Fused4<PREC, LOG2N, LOG2R, false>;
-  const int per_block = K::SMEM + 1024;
-  int carve = (int)((100LL * per_block * (K::MINB > 0 ? K::MINB : 1) + 228 * 1024 - 1) / (228 * 1024));
-  carve = carve < 1 ? 1 : carve > 100 ? 100 : carve;
+  const int carve = carveout_for(K::SMEM, K::MINB);
   for (auto kern : {fused4_fft_kernel<PREC, LOG2N, LOG2R, false>, fused4_fft_kernel<PREC, LOG2N, LOG2R, true>}) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, carve);
     if (e != cudaSuccess) return e;

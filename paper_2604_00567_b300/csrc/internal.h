@@ -12,6 +12,16 @@ namespace dsfft {
 
 enum Prec : int { kFP32 = 0, kFP16 = 1, kBF16 = 2 };
 
+// Shared-memory carveout (percent of the SM's 228 KB maximum) that holds
+// `blocks` resident blocks of `smem` dynamic bytes (plus the 1 KB the runtime
+// reserves per block).  What the blocks do not need stays L1, where the
+// per-lane twiddle loads of the large-N kernels hit.
+inline int carveout_for(int smem, int blocks) {
+  const long long need = (long long)(smem + 1024) * (blocks > 0 ? blocks : 1);
+  const int carve = (int)((100LL * need + 228 * 1024 - 1) / (228 * 1024));
+  return carve < 1 ? 1 : carve > 100 ? 100 : carve;
+}
+
 // One transform of a mixed batch: device pointers to its input and output.
 struct BatchItem {
   const void *in;

@@ -341,20 +341,27 @@ cudaError_t launch_sweep_one(const void *in, void *out, const BatchItem *items, 
   return cudaGetLastError();
 }
 
+// Carveout: the shared memory of the blocks that can reside (registers,
+// threads and shared memory decide); the rest stays L1 for the per-lane
+// twiddles (measured on B300: FP16 N = 2^18 28.7 % of HBM against 26.2 %
+// with the maximum carveout, FP32 2^18 30.3 against 26.6 %).
 template <class F>
-cudaError_t prepare_sweep_kernel(F kern, int smem) {
+cudaError_t prepare_sweep_kernel(F kern, int smem, int tpb) {
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  int nblk = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nblk, kern, tpb, smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, carveout_for(smem, nblk));
 }
 
 template <int PREC, int LS, bool SCALED, bool LAST, bool R4>
 cudaError_t prepare_sweep_one() {
   using K = Sweep<PREC, LS, SCALED, LAST, R4>;
   using E = typename K::E;
-  cudaError_t e = prepare_sweep_kernel(sweep_fft_kernel<PREC, LS, SCALED, LAST, ContigIO<E>, R4>, K::SMEM);
+  cudaError_t e = prepare_sweep_kernel(sweep_fft_kernel<PREC, LS, SCALED, LAST, ContigIO<E>, R4>, K::SMEM, K::TPB);
   if (e != cudaSuccess) return e;
-  return prepare_sweep_kernel(sweep_fft_kernel<PREC, LS, SCALED, LAST, GatherIO<E>, R4>, K::SMEM);
+  return prepare_sweep_kernel(sweep_fft_kernel<PREC, LS, SCALED, LAST, GatherIO<E>, R4>, K::SMEM, K::TPB);
 }
 
 using SweepFn = cudaError_t (*)(const void *, void *, const BatchItem *, int64_t, int, int, const uint4 *,

@@ -93,7 +93,7 @@ def test_autotune_sweep_split_cached(dsfft, tmp_path, monkeypatch):
     monkeypatch.setenv("DSFFT_AUTOTUNE_CACHE", str(cache))
     p1 = dsfft.Plan(1 << 18, "fp16", "dual_select", autotune=True)
     i1 = p1.info()
-    assert i1["autotuned"] == 1 and i1["variant_name"] == "sweeps" and 8 <= i1["sweep_passes"] <= 10
+    assert i1["autotuned"] == 1 and i1["variant_name"] == "sweeps" and 7 <= i1["sweep_passes"] <= 11
     data = json.loads(cache.read_text())
     key = [k for k in data if k.endswith("|1|18|2")][0]
     data[key] = 4 * 100 + 10          # sweeps with 10 passes in sweep 1
