@@ -14,12 +14,22 @@ enum Prec : int { kFP32 = 0, kFP16 = 1, kBF16 = 2 };
 
 // Shared-memory carveout (percent of the SM's 228 KB maximum) that holds
 // `blocks` resident blocks of `smem` dynamic bytes (plus the 1 KB the runtime
-// reserves per block).  What the blocks do not need stays L1, where the
-// per-lane twiddle loads of the large-N kernels hit.
+// reserves per block).  The runtime picks the smallest shared-memory
+// configuration of the SM (0, 8, 16, 32, 64, 100, 132, 164, 196 or 228 KB on
+// this architecture) at or above the percentage, so the percentage is that of
+// the smallest configuration that fits, rounded down.  What the blocks do not
+// need stays L1, where the per-lane twiddle loads of the large-N kernels hit.
 inline int carveout_for(int smem, int blocks) {
+  static const int kConfigKB[] = {0, 8, 16, 32, 64, 100, 132, 164, 196, 228};
   const long long need = (long long)(smem + 1024) * (blocks > 0 ? blocks : 1);
-  const int carve = (int)((100LL * need + 228 * 1024 - 1) / (228 * 1024));
-  return carve < 1 ? 1 : carve > 100 ? 100 : carve;
+  int kb = 228;
+  for (int c : kConfigKB)
+    if (1024LL * c >= need) {
+      kb = c;
+      break;
+    }
+  const int carve = (int)(100LL * kb / 228);
+  return carve < 1 ? 1 : carve;
 }
 
 // One transform of a mixed batch: device pointers to its input and output.
