@@ -243,6 +243,29 @@ int cluster_log2k(int prec, int log2n) {
   return log2n == 15 ? 2 : log2n == 16 ? 3 : log2n == 17 ? 3 : -1;
 }
 
+// Launched with the load-balancing cluster scheduling policy (the hardware
+// may place a cluster's CTAs by SM load rather than spreading them): measured
+// on B300, FP16 N = 2^16 41.0 -> 41.8 % of HBM, 2^15 45.5 -> 46.8 %, FP32
+// 2^15 49.3 -> 50.1 %, against the default policy.
+template <int PREC, int LOG2N, int LOG2K, bool SCALED, class IO>
+static cudaError_t launch_cluster_io(const IO &io, int64_t blocks, int64_t batch, const uint4 *twp,
+                                     const Stage0Twiddles &tw0, int *status, uint32_t tx_extra,
+                                     cudaStream_t stream) {
+  using K = Clus<PREC, LOG2N, LOG2K, SCALED>;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)blocks);
+  cfg.blockDim = dim3(K::TPB);
+  cfg.dynamicSmemBytes = K::SMEM;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterSchedulingPolicyPreference;
+  attr[0].val.clusterSchedulingPolicyPreference = cudaClusterSchedulingPolicyLoadBalancing;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, cluster_fft_kernel<PREC, LOG2N, LOG2K, SCALED, IO>, io, batch, twp, tw0, status,
+                            tx_extra);
+}
+
 template <int PREC, int LOG2N, int LOG2K, bool SCALED>
 static cudaError_t launch_cluster_one(const void *in, void *out, const BatchItem *items, int64_t batch,
                                       const uint4 *twp, const Stage0Twiddles &tw0, int *status,
@@ -251,14 +274,12 @@ static cudaError_t launch_cluster_one(const void *in, void *out, const BatchItem
   using E = typename K::E;
   const int64_t blocks = batch * K::K;
   if (blocks > 0x7FFFFFFF) return cudaErrorInvalidConfiguration;
-  if (items) {
-    cluster_fft_kernel<PREC, LOG2N, LOG2K, SCALED, GatherIO<E>><<<(unsigned)blocks, K::TPB, K::SMEM, stream>>>(
-        GatherIO<E>{items}, batch, twp, tw0, status, tx_extra);
-  } else {
-    cluster_fft_kernel<PREC, LOG2N, LOG2K, SCALED, ContigIO<E>><<<(unsigned)blocks, K::TPB, K::SMEM, stream>>>(
-        ContigIO<E>{static_cast<const E *>(in), static_cast<E *>(out), K::N}, batch, twp, tw0, status, tx_extra);
-  }
-  return cudaGetLastError();
+  if (items)
+    return launch_cluster_io<PREC, LOG2N, LOG2K, SCALED>(GatherIO<E>{items}, blocks, batch, twp, tw0, status,
+                                                         tx_extra, stream);
+  return launch_cluster_io<PREC, LOG2N, LOG2K, SCALED>(
+      ContigIO<E>{static_cast<const E *>(in), static_cast<E *>(out), K::N}, blocks, batch, twp, tw0, status,
+      tx_extra, stream);
 }
 
 // Carveout: the shared memory of the CTAs the register budget lets reside
