@@ -265,8 +265,22 @@ struct Sweep {
 
 // Sweep 1 reads io.src and writes io.dst; sweep 2 (LAST) reads and writes
 // io.dst in place.
+// Resident blocks per SM the register allocation must allow (0: the
+// compiler's choice).  The unscaled FP16 first sweep in blocks of fewer
+// than 1024 threads compiles to 72-84 registers when left alone, so fewer
+// than 1024 threads stay resident; the floor of 1024 (64 registers, no
+// spills) measured faster on B300 (FP16 inverse, unscaled: 2^18 25.3 ->
+// 29.4 %, 2^19 22.1 -> 24.9 % of HBM).  Elsewhere the compiler's choice
+// (at most 64 registers already) measured as fast or faster than a stated
+// minimum.
+template <int PREC, int LS, bool SCALED, bool LAST, bool R4>
+__host__ __device__ constexpr int sweep_minb() {
+  return PREC == kFP16 && !SCALED && !LAST && Sweep<PREC, LS, SCALED, LAST, R4>::TPB < 1024
+             ? 1024 / Sweep<PREC, LS, SCALED, LAST, R4>::TPB
+             : 0;
+}
 template <int PREC, int LS, bool SCALED, bool LAST, class IO, bool R4 = false>
-__global__ void __launch_bounds__(Sweep<PREC, LS, SCALED, LAST, R4>::TPB)
+__global__ void __launch_bounds__(Sweep<PREC, LS, SCALED, LAST, R4>::TPB, (sweep_minb<PREC, LS, SCALED, LAST, R4>()))
     sweep_fft_kernel(const IO io, int64_t batch, int log2n, int P0, const uint4 *__restrict__ twp,
                      const uint4 r2e, const uint32_t sgn_bits) {
   using K = Sweep<PREC, LS, SCALED, LAST, R4>;
