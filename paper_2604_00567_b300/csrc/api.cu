@@ -30,6 +30,8 @@ struct fft_plan {
   uint4 *table[2];      // packed tables (N/2 entries), [0] forward, [1] inverse
   uint4 *twp[2];        // per-pass copies (N - 1 entries) read by the kernels
   Stage0Twiddles tw0[2];  // host copy of the first min(N, 32) - 1 per-pass entries
+  Phase1Twiddles tw1[2];  // FP32 N = 2^15, 2^16: host copy of the first 255 per-pass entries
+  bool has_tw1;           // tw1 filled (FP32 plans of the cluster sizes)
   int kernel;           // 0 fused, 1 sweeps, 2 cluster
   bool narrow;          // fused: half-width register block
   int variant;          // fft_variant
@@ -149,8 +151,9 @@ cudaError_t plan_launch(const fft_plan *p, const void *in, void *out, int64_t ba
   if (p->kernel == 0)
     return launch_fused(p->prec, p->log2n, p->narrow, scaled, in, out, batch, p->twp[d], p->tw0[d], stream);
   if (p->kernel == 2)
-    return launch_cluster(p->prec, p->log2n, scaled, in, out, nullptr, batch, p->twp[d], p->tw0[d], p->status,
-                          p->fault_tx, stream);
+    return launch_cluster(p->prec, p->log2n, scaled, in, out, nullptr, batch, p->twp[d], p->tw0[d],
+                          p->has_tw1 ? &p->tw1[d] : nullptr,
+                          p->status, p->fault_tx, stream);
   return launch_sweeps(p->prec, p->log2n, scaled, in, out, nullptr, batch, p->twp[d], stream, p->sweep_ls1);
 }
 
@@ -313,6 +316,8 @@ bool dsfft::plan_view(const fft_plan *p, PlanView *v) {
   v->twp[1] = p->twp[1];
   v->tw0[0] = &p->tw0[0];
   v->tw0[1] = &p->tw0[1];
+  v->tw1[0] = p->has_tw1 ? &p->tw1[0] : nullptr;
+  v->tw1[1] = p->has_tw1 ? &p->tw1[1] : nullptr;
   v->radix = p->radix;
   v->sweep_ls1 = p->sweep_ls1;
   v->status = p->status;
@@ -394,7 +399,7 @@ cudaError_t batch_enqueue(const fft_batch *b, cudaStream_t stream) {
     cudaStream_t st = nside > 0 ? b->side[k % nside] : stream;
     if (p->kernel == 2)
       e = launch_cluster(p->prec, p->log2n, scaled, nullptr, nullptr, b->d_items + g.first, g.count, p->twp[g.dir],
-                         p->tw0[g.dir], p->status, p->fault_tx, st);
+                         p->tw0[g.dir], p->has_tw1 ? &p->tw1[g.dir] : nullptr, p->status, p->fault_tx, st);
     else
       e = launch_sweeps(p->prec, p->log2n, scaled, nullptr, nullptr, b->d_items + g.first, g.count, p->twp[g.dir],
                         st, p->sweep_ls1);
@@ -523,6 +528,7 @@ fft_status fft_plan_create(fft_plan **plan, int64_t n, fft_precision prec, fft_f
   const size_t tw_bytes = sizeof(uint2);
   int *counts = nullptr;
   uint4 *head = nullptr;      // 16-byte forms of the first-stage entries: [dir][radix 2/4][31]
+  uint4 *head1 = nullptr;     // FP32 cluster sizes: 16-byte forms of the phase-1 entries: [dir][255]
   cudaStream_t st = nullptr;
   fft_status status = FFT_OK;
   int host_counts[2] = {0, 0};
@@ -546,6 +552,15 @@ fft_status fft_plan_create(fft_plan **plan, int64_t n, fft_precision prec, fft_f
       e = cudaMemcpyAsync(p->tw0[d].e, head + d * 62, (size_t)cnt0 * sizeof(uint4), cudaMemcpyDeviceToHost, st);
     }
     if (e != cudaSuccess) { status = cuda_fail(e, "per-pass table"); break; }
+    p->has_tw1 = prec == kFP32 && cluster_log2k(prec, log2n) >= 0;
+    if (p->has_tw1) {
+      if ((e = device_alloc(&head1, 2 * 255 * sizeof(uint4))) != cudaSuccess) { status = cuda_fail(e, "cudaMalloc"); break; }
+      for (int d = 0; d < 2 && e == cudaSuccess; ++d) {
+        if ((e = launch_per_pass_table(log2n, p->table[d], head1 + d * 255, 255, 0, st)) != cudaSuccess) break;
+        e = cudaMemcpyAsync(p->tw1[d].e, head1 + d * 255, 255 * sizeof(uint4), cudaMemcpyDeviceToHost, st);
+      }
+      if (e != cudaSuccess) { status = cuda_fail(e, "phase-1 twiddles"); break; }
+    }
     if ((e = cudaMemcpyAsync(host_counts, counts, 2 * sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess) { status = cuda_fail(e, "copy counts"); break; }
     if (radix == 4) {
       const int64_t c4 = 3 * n / 4, p4 = n - 1 - (log2n & 1);
@@ -590,6 +605,7 @@ fft_status fft_plan_create(fft_plan **plan, int64_t n, fft_precision prec, fft_f
   if (st) cudaStreamDestroy(st);
   if (counts) cudaFree(counts);
   if (head) cudaFree(head);
+  if (head1) cudaFree(head1);
   if (status != FFT_OK) {
     for (int d = 0; d < 2; ++d) {
       if (p->table[d]) cudaFree(p->table[d]);

@@ -67,7 +67,13 @@ struct Clus {
   static constexpr int GC2 = M1 / K;     // phase-2 groups per CTA
   // remainder stage first where measured faster: phase 2 always (its first
   // stage then shares twiddles across columns), phase 1 for FP32 only
-  using P1 = GroupPasses<PREC, LS1, 0, SCALED, PREC == kFP32>;
+  // FP32: every phase-1 twiddle from the kernel parameters (Phase1Twiddles;
+  // measured faster, FP32 2^16 39.6 -> 41.9 % of HBM); FP16/BF16: only the
+  // first stage's (reading the later ones from the constant bank measured
+  // slower there, 41.9 -> 38.7 %)
+  static constexpr bool TW0_ALL = PREC == kFP32;
+  using TwParams = typename std::conditional<TW0_ALL, Phase1Twiddles, Stage0Twiddles>::type;
+  using P1 = GroupPasses<PREC, LS1, 0, SCALED, PREC == kFP32, TW0_ALL>;
   using P2 = GroupPasses<PREC, LS2, LS1, SCALED, true>;
   static constexpr int R = P1::R;
   static constexpr int TPB = GC1 * P1::T;
@@ -84,6 +90,8 @@ struct Clus {
   static_assert(K <= 8, "portable cluster size");
   static_assert(LS1 > P1::LOG2R, "phase 1 has an exchange before its last stage");
   static_assert(GC2 >= (1 << P1::LAST_PL), "a phase-1 output's owner depends only on its compile-time part");
+  static_assert(!TW0_ALL || (1 << LS1) - 1 <= (int)(sizeof(Phase1Twiddles) / sizeof(uint4)),
+                "the phase-1 table fits the parameters");
 };
 
 // Asynchronous remote stores whose arrival the destination CTA counts on
@@ -138,7 +146,8 @@ template <int PREC, int LOG2N, int LOG2K, bool SCALED, class IO>
 __global__ void __cluster_dims__(1 << LOG2K, 1, 1)
     __launch_bounds__(Clus<PREC, LOG2N, LOG2K, SCALED>::TPB, Clus<PREC, LOG2N, LOG2K, SCALED>::MINB)
     cluster_fft_kernel(const IO io, int64_t batch, const uint4 *__restrict__ twp,
-                       const __grid_constant__ Stage0Twiddles tw0, int *status, uint32_t tx_extra) {
+                       const __grid_constant__ typename Clus<PREC, LOG2N, LOG2K, SCALED>::TwParams tw0, int *status,
+                       uint32_t tx_extra) {
   using K = Clus<PREC, LOG2N, LOG2K, SCALED>;
   using E = typename K::E;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -249,8 +258,8 @@ int cluster_log2k(int prec, int log2n) {
 // 2^15 49.3 -> 50.1 %, against the default policy.
 template <int PREC, int LOG2N, int LOG2K, bool SCALED, class IO>
 static cudaError_t launch_cluster_io(const IO &io, int64_t blocks, int64_t batch, const uint4 *twp,
-                                     const Stage0Twiddles &tw0, int *status, uint32_t tx_extra,
-                                     cudaStream_t stream) {
+                                     const typename Clus<PREC, LOG2N, LOG2K, SCALED>::TwParams &tw0, int *status,
+                                     uint32_t tx_extra, cudaStream_t stream) {
   using K = Clus<PREC, LOG2N, LOG2K, SCALED>;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)blocks);
@@ -268,12 +277,21 @@ static cudaError_t launch_cluster_io(const IO &io, int64_t blocks, int64_t batch
 
 template <int PREC, int LOG2N, int LOG2K, bool SCALED>
 static cudaError_t launch_cluster_one(const void *in, void *out, const BatchItem *items, int64_t batch,
-                                      const uint4 *twp, const Stage0Twiddles &tw0, int *status,
-                                      uint32_t tx_extra, cudaStream_t stream) {
+                                      const uint4 *twp, const Stage0Twiddles &tw0s, const Phase1Twiddles *tw1,
+                                      int *status, uint32_t tx_extra, cudaStream_t stream) {
   using K = Clus<PREC, LOG2N, LOG2K, SCALED>;
   using E = typename K::E;
   const int64_t blocks = batch * K::K;
   if (blocks > 0x7FFFFFFF) return cudaErrorInvalidConfiguration;
+  const typename K::TwParams *tw0p;
+  if constexpr (K::TW0_ALL) {
+    if (!tw1) return cudaErrorInvalidValue;
+    tw0p = tw1;
+  } else {
+    (void)tw1;
+    tw0p = &tw0s;
+  }
+  const typename K::TwParams &tw0 = *tw0p;
   if (items)
     return launch_cluster_io<PREC, LOG2N, LOG2K, SCALED>(GatherIO<E>{items}, blocks, batch, twp, tw0, status,
                                                          tx_extra, stream);
@@ -320,13 +338,13 @@ cudaError_t prepare_cluster(int prec, int log2n) {
 }
 
 cudaError_t launch_cluster(int prec, int log2n, bool scaled, const void *in, void *out, const BatchItem *items,
-                           int64_t batch, const uint4 *twp, const Stage0Twiddles &tw0, int *status,
-                           uint32_t tx_extra, cudaStream_t stream) {
+                           int64_t batch, const uint4 *twp, const Stage0Twiddles &tw0, const Phase1Twiddles *tw1,
+                           int *status, uint32_t tx_extra, cudaStream_t stream) {
   if (!status) return cudaErrorInvalidValue;
-#define DSFFT_CL(P, L, LK)                                                                                 \
-  case P * 100 + L:                                                                                        \
-    return scaled ? launch_cluster_one<P, L, LK, true>(in, out, items, batch, twp, tw0, status, tx_extra, stream)   \
-                  : launch_cluster_one<P, L, LK, false>(in, out, items, batch, twp, tw0, status, tx_extra, stream);
+#define DSFFT_CL(P, L, LK)                                                                                          \
+  case P * 100 + L:                                                                                                 \
+    return scaled ? launch_cluster_one<P, L, LK, true>(in, out, items, batch, twp, tw0, tw1, status, tx_extra, stream) \
+                  : launch_cluster_one<P, L, LK, false>(in, out, items, batch, twp, tw0, tw1, status, tx_extra, stream);
   switch (prec * 100 + log2n) {
     DSFFT_CL(kFP32, 15, 2)
     DSFFT_CL(kFP32, 16, 3)

@@ -17,7 +17,9 @@
 
 namespace dsfft {
 
-template <int PREC, int LS, int P0, bool SCALED, bool REM_FIRST = true>
+// TW0_ALL (P0 = 0 only): every pass's twiddles come from tw0 (the whole
+// phase-1 table in the constant bank), not only the first stage's.
+template <int PREC, int LS, int P0, bool SCALED, bool REM_FIRST = true, bool TW0_ALL = false>
 struct GroupPasses {
   using E = typename Elem<PREC>::T;
   static constexpr int LOG2R = PREC == kFP32 ? 4 : 5;
@@ -41,7 +43,7 @@ struct GroupPasses {
   static constexpr int LAST_PL = stage_start(NSTAGES - 1);   // first local pass of the last stage
 
   // tw0(i): per-pass entry i for the first register stage when P0 = 0 (the
-  // same for every thread: the constant bank).  Depth-first order over the
+  // same for every thread: the constant bank), for every stage with TW0_ALL.  Depth-first order over the
   // stage's passes (as in fused.cuh): pass I on a block of registers, then
   // its two halves, on columns [CB, CB + CN) (CN > 1 when those columns
   // share j_loc, hence every twiddle).
@@ -52,8 +54,9 @@ struct GroupPasses {
     constexpr int half = 1 << (RHO - 1 - I);
     constexpr int ql = bitrev(QTOP >> (RHO - I), I);
     constexpr int p = P0 + PL + I;                     // global pass
+    static_assert(!TW0_ALL || P0 == 0, "the constant-bank table holds the passes from 0");
     uint4 e;
-    if constexpr (P0 == 0 && PL == 0) e = tw0(((1 << I) - 1) + ql);
+    if constexpr (P0 == 0 && (PL == 0 || TW0_ALL)) e = tw0(((1 << p) - 1) + jloc + (ql << PL));
     else e = tw_load<PREC>(twp, ((1 << p) - 1) + jg + (jloc << P0) + (ql << (PL + P0)));
     if constexpr (PREC != kFP32 && P0 == 0 && PL == 0 && half * CN >= 4) {
       // first stage: e is the same in every lane, so a uniform branch on

@@ -107,6 +107,15 @@ struct Stage0Twiddles {
   uint4 e[31];
 };
 
+// Twiddles of every phase-1 pass of the FP32 cluster kernel (passes 0 .. 7
+// of N = 2^15 and 2^16: the first 255 per-pass entries, the same for every
+// CTA), passed by value like Stage0Twiddles.  The FP16/BF16 cluster kernels
+// read their later phase-1 twiddles from the per-pass table instead (measured
+// faster there).
+struct Phase1Twiddles {
+  uint4 e[255];
+};
+
 // Fused on-chip transform of `batch` signals of length 2^log2n.  `twp` is
 // the device per-pass table, `tw0` its first entries.
 cudaError_t launch_fused(int prec, int log2n, bool narrow, bool scaled, const void *in, void *out, int64_t batch,
@@ -140,13 +149,14 @@ cudaError_t launch_sweeps4(int prec, int log2n, bool scaled, int inverse, const 
 // transform between the two halves of the passes.  -1 = not handled.
 int cluster_log2k(int prec, int log2n);
 cudaError_t prepare_cluster(int prec, int log2n);
-// `tw0`: the first per-pass entries (the fused kernel's stage-0 twiddles).
+// `tw0`: the first per-pass entries (the fused kernel's stage-0 twiddles);
+// `tw1`: every phase-1 entry (FP32 only, required there).
 // `status`: device word whose bit 1 a CTA sets when its bounded wait for
 // the phase-1 data gives up (the FP16/BF16 kernels); `tx_extra`
 // (fault injection, normally 0) is added to the bytes that wait expects.
 cudaError_t launch_cluster(int prec, int log2n, bool scaled, const void *in, void *out, const BatchItem *items,
-                           int64_t batch, const uint4 *twp, const Stage0Twiddles &tw0, int *status,
-                           uint32_t tx_extra, cudaStream_t stream);
+                           int64_t batch, const uint4 *twp, const Stage0Twiddles &tw0, const Phase1Twiddles *tw1,
+                           int *status, uint32_t tx_extra, cudaStream_t stream);
 
 // Read-only view of a plan's launch parameters (for entry points outside
 // api.cu); false for a null plan.
@@ -155,6 +165,7 @@ struct PlanView {
   int scale[2];
   const uint4 *twp[2];
   const Stage0Twiddles *tw0[2];   // host copies of the first per-pass entries
+  const Phase1Twiddles *tw1[2];   // FP32 cluster plans: every phase-1 entry (else null)
   int radix;                      // 2 or 4
   int sweep_ls1;                  // passes in sweep 1 (0: ceil(m/2))
   int *status;                    // device error word of the bounded waits

@@ -280,8 +280,8 @@ extern "C" fft_status fft_exec_batch_noalloc(const fft_noalloc_item *items, int6
     if (k.view.kernel != 0) {
       const bool scaled = k.view.scale[k.dir] != 0;
       e = k.view.kernel == 2 ? launch_cluster(k.view.prec, k.view.log2n, scaled, nullptr, nullptr, d_items + i,
-                                              j - i, k.view.twp[k.dir], *k.view.tw0[k.dir], k.view.status,
-                                              k.view.fault_tx, st)
+                                              j - i, k.view.twp[k.dir], *k.view.tw0[k.dir], k.view.tw1[k.dir],
+                                              k.view.status, k.view.fault_tx, st)
                              : launch_sweeps(k.view.prec, k.view.log2n, scaled, nullptr, nullptr, d_items + i, j - i,
                                              k.view.twp[k.dir], st, k.view.sweep_ls1);
       if (e != cudaSuccess) return cuda_fail(e, "large-size launch");
