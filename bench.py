@@ -534,6 +534,15 @@ def serve_measure(seconds: float = 1.0, rate: float = 20000.0, budget: int = 40_
             r = dsfft.Server.request(pools[prec], n, prec, tag=k)
             r.count = int(sig[k])
             reqs.append(r)
+        # warm-up: the first tenth of the trace (at most 1000 requests),
+        # drained and discarded, so that the measured replay starts from a
+        # server whose streams, arena and scheduler have already run
+        nw = min(1000, max(1, len(reqs) // 10))
+        srv.replay(reqs[:nw], arrivals[:nw], keep=pools)
+        srv.drain(600.0)
+        while srv.poll(65536):
+            pass
+        ticks0 = srv.stats()["ticks"]
         srv.replay(reqs, arrivals, keep=pools)
         srv.drain(600.0)
         done = []
@@ -561,14 +570,15 @@ def serve_measure(seconds: float = 1.0, rate: float = 20000.0, budget: int = 40_
     return {
         "config": "open-loop Poisson trace %.0f req/s for %.1f s (seed 2), U{1..256} signals, N = 2^U{8..18}, "
                   "FP32/FP16 p=0.5 (dual_select), inputs resident on the device, 40 GB arena, "
-                  "outputs freed at completion, ticks of at most %d MiB of output, %d ticks in flight"
+                  "outputs freed at completion, ticks of at most %d MiB of output, %d ticks in flight, "
+                  "after a warm-up replay of the trace's first tenth"
                   % (rate, seconds, max_tick_bytes >> 20, in_flight),
         "requests": len(arrivals), "completed_ok": len(ok),
         "p50_ms": round(float(np.percentile(lat_ms, 50)), 3), "p99_ms": round(float(np.percentile(lat_ms, 99)), 3),
         "max_ms": round(float(lat_ms.max()), 3), "mean_ms": round(float(lat_ms.mean()), 3),
         "requests_per_s": len(ok) / span, "transforms_per_s": transforms / span,
         "algorithmic_GB_per_s": round(payload / span / 1e9, 1),
-        "ticks": st["ticks"], "requests_per_tick": round(len(ok) / max(1, st["ticks"]), 2),
+        "ticks": st["ticks"] - ticks0, "requests_per_tick": round(len(ok) / max(1, st["ticks"] - ticks0), 2),
         "arena_peak_GB": round(st["arena_peak"] / 1e9, 3), "plans": st["plans"],
         "wall_s": round(span, 3),
     }

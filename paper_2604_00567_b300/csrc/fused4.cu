@@ -52,14 +52,23 @@ static cudaError_t prepare4_one() {
   return cudaSuccess;
 }
 
+template <int PREC, int LOG2N>
+static FusedShape shape4_one() {
+  constexpr int LOG2R = r4_log2r(LOG2N);
+  using K = Fused4<PREC, LOG2N, LOG2R, false>;
+  return FusedShape{LOG2R, K::T, K::TPC, K::TPB, K::SMEM};
+}
+
 using Launch4Fn = cudaError_t (*)(const void *, void *, int64_t, const uint4 *, const Stage0R4 &, int, cudaStream_t);
 using Prepare4Fn = cudaError_t (*)();
+using Shape4Fn = FusedShape (*)();
 
 template <int PREC, int... L>
 struct Table4 {
   static constexpr Launch4Fn plain[] = {launch4_one<PREC, L, false>...};
   static constexpr Launch4Fn scaled[] = {launch4_one<PREC, L, true>...};
   static constexpr Prepare4Fn prepare[] = {prepare4_one<PREC, L>...};
+  static constexpr Shape4Fn shape[] = {shape4_one<PREC, L>...};
 };
 
 #define DSFFT_LOG2N_LIST4 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14
@@ -69,14 +78,8 @@ using T4_B16 = Table4<kBF16, DSFFT_LOG2N_LIST4>;
 
 FusedShape fused4_shape(int prec, int log2n) {
   if (log2n < 1 || log2n > kFusedMaxLog2N) return FusedShape{0, 0, 0, 0, 0};
-  const int r = r4_log2r(log2n);
-  const int t = 1 << (log2n - r);
-  const int bth = t >= 256 ? t : 256;
-  const int tpc = bth / t;
-  const int eb = prec == kFP32 ? 8 : 4;
-  const int stages_gt1 = r4_stage_levels(log2n, r, 0) < log2n;
-  const int padn = (1 << log2n) + ((1 << log2n) >> (eb == 8 ? 4 : 5));   // Fused::PADN
-  return FusedShape{r, t, tpc, t * tpc, stages_gt1 ? tpc * padn * eb : 0};
+  const int i = log2n - 1;
+  return prec == kFP32 ? T4_32::shape[i]() : prec == kFP16 ? T4_16::shape[i]() : T4_B16::shape[i]();
 }
 
 cudaError_t prepare_fused4(int prec, int log2n) {
