@@ -31,7 +31,8 @@
 // a warp (same output o, consecutive g) fill 32 consecutive elements of one
 // owner's group.  The first register stage of phase 1 (passes 0..4, the
 // same twiddles for every thread) reads its twiddles from the kernel
-// parameters (constant bank).
+// parameters (constant bank); for FP32 every phase-1 stage does (the lanes
+// of a warp, consecutive groups of one thread index, share each twiddle).
 #include <cooperative_groups.h>
 
 #include "group.cuh"
