@@ -130,6 +130,9 @@ cudaError_t launch_fused_tma(int prec, int log2n, bool scaled, const void *in, v
 // `in` and `out` must differ; sweep 2 runs in place on `out`.
 void sweep_split(int log2n, int *ls1, int *ls2);
 bool sweep_ls1_valid(int log2n, int ls1);
+// SMs of the current device (cached per device; 0 when unknown): the sweeps
+// switch to their narrow-group kernels below one block per SM.
+int sweep_sm_count();
 cudaError_t prepare_sweeps(int prec, int log2n, int ls1 = 0);
 // `items` (device array, one per transform) replaces in/out when non-null.
 cudaError_t launch_sweeps(int prec, int log2n, bool scaled, const void *in, void *out, const BatchItem *items,

@@ -1,6 +1,8 @@
 // sweep.cu — host dispatch of the two-sweep FFT for N > 2^14 (the kernels
 // are in sweep.cuh, instantiated per precision by sweep_fp32.cu,
 // sweep_fp16.cu and sweep_bf16.cu).
+#include <atomic>
+
 #include "internal.h"
 
 namespace dsfft {
@@ -17,6 +19,21 @@ extern template SweepFn sweep_lookup<kBF16>(bool, bool, bool, int);
 extern template cudaError_t sweep_prepare_ls<kFP32>(bool, int);
 extern template cudaError_t sweep_prepare_ls<kFP16>(bool, int);
 extern template cudaError_t sweep_prepare_ls<kBF16>(bool, int);
+
+int sweep_sm_count() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  const bool cached = dev >= 0 && dev < 64;
+  if (cached) {
+    const int v = cache[dev].load(std::memory_order_relaxed);
+    if (v > 0) return v;
+  }
+  int v = 0;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (cached) cache[dev].store(v, std::memory_order_relaxed);
+  return v;
+}
 
 void sweep_split(int log2n, int *ls1, int *ls2) {
   *ls1 = (log2n + 1) / 2;

@@ -34,7 +34,10 @@ __device__ __forceinline__ void sw_stcs(uint32_t *p, uint32_t v) { __stcs(reinte
 // R4: radix-4 passes (the radix-4 extension, fused4.cuh): stages of whole
 // radix-4 passes with 16 points per thread; an odd LS (sweep 1 of an odd
 // log2 N) starts with the radix-2 pass of span 1.
-template <int PREC, int LS, bool SCALED, bool LAST, bool R4 = false>
+// GSHIFT: a block of 2^GSHIFT times fewer groups (at least 4) than the
+// default, for launches with fewer blocks than the GPU has SMs (one or a few
+// transforms): shorter runs per warp, more blocks.
+template <int PREC, int LS, bool SCALED, bool LAST, bool R4 = false, int GSHIFT = 0>
 struct Sweep {
   using E = typename Elem<PREC>::T;
   static constexpr int EB = (int)sizeof(E);
@@ -44,7 +47,9 @@ struct Sweep {
   static constexpr int T = M / R;                        // threads per group
   // groups per block: at most 32, and at most 1024 threads (R points each)
   static constexpr int LOG2G_CAP = (LOG2R == 4 ? 14 : 15) - LS;
-  static constexpr int LOG2G = LOG2G_CAP < 5 ? LOG2G_CAP : 5;
+  static constexpr int LOG2G_DEF = LOG2G_CAP < 5 ? LOG2G_CAP : 5;
+  static constexpr int LOG2G_MIN = LOG2G_DEF < 2 ? LOG2G_DEF : 2;
+  static constexpr int LOG2G = LOG2G_DEF - GSHIFT > LOG2G_MIN ? LOG2G_DEF - GSHIFT : LOG2G_MIN;
   static constexpr int G = 1 << LOG2G;
   static constexpr int TPB = G * T;
   static_assert(TPB <= 1024, "one block holds at most 1024 threads");
@@ -273,17 +278,18 @@ struct Sweep {
 // 29.4 %, 2^19 22.1 -> 24.9 % of HBM).  Elsewhere the compiler's choice
 // (at most 64 registers already) measured as fast or faster than a stated
 // minimum.
-template <int PREC, int LS, bool SCALED, bool LAST, bool R4>
+template <int PREC, int LS, bool SCALED, bool LAST, bool R4, int GSHIFT>
 __host__ __device__ constexpr int sweep_minb() {
-  return PREC == kFP16 && !SCALED && !LAST && Sweep<PREC, LS, SCALED, LAST, R4>::TPB < 1024
-             ? 1024 / Sweep<PREC, LS, SCALED, LAST, R4>::TPB
+  return PREC == kFP16 && !SCALED && !LAST && Sweep<PREC, LS, SCALED, LAST, R4, GSHIFT>::TPB < 1024
+             ? 1024 / Sweep<PREC, LS, SCALED, LAST, R4, GSHIFT>::TPB
              : 0;
 }
-template <int PREC, int LS, bool SCALED, bool LAST, class IO, bool R4 = false>
-__global__ void __launch_bounds__(Sweep<PREC, LS, SCALED, LAST, R4>::TPB, (sweep_minb<PREC, LS, SCALED, LAST, R4>()))
+template <int PREC, int LS, bool SCALED, bool LAST, class IO, bool R4 = false, int GSHIFT = 0>
+__global__ void __launch_bounds__(Sweep<PREC, LS, SCALED, LAST, R4, GSHIFT>::TPB,
+                                  (sweep_minb<PREC, LS, SCALED, LAST, R4, GSHIFT>()))
     sweep_fft_kernel(const IO io, int64_t batch, int log2n, int P0, const uint4 *__restrict__ twp,
                      const uint4 r2e, const uint32_t sgn_bits) {
-  using K = Sweep<PREC, LS, SCALED, LAST, R4>;
+  using K = Sweep<PREC, LS, SCALED, LAST, R4, GSHIFT>;
   using E = typename K::E;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   E *sm = reinterpret_cast<E *>(smem_raw);
@@ -344,6 +350,21 @@ cudaError_t launch_sweep_one(const void *in, void *out, const BatchItem *items, 
   if (S < K::G) return cudaErrorInvalidValue;
   const int64_t blocks = batch * (S >> K::LOG2G);
   if (blocks > 0x7FFFFFFF) return cudaErrorInvalidConfiguration;
+  if constexpr (!R4) {
+    // at most one block per two SMs (one or a few transforms): the
+    // narrow-group kernel, which spreads the same work over up to 4x the
+    // blocks (measured on B300, batch 1: FP16 2^20 5.0 -> 7.6 %, 2^21 9.0
+    // -> 11.8 %, FP32 2^18 3.3 -> 4.4 % of HBM; switching already below one
+    // block per SM cost FP16 2^22 and FP32 2^21 2-4 points)
+    using KS = Sweep<PREC, LS, SCALED, LAST, R4, 2>;
+    if (!items && KS::LOG2G < K::LOG2G && 2 * blocks <= sweep_sm_count()) {
+      sweep_fft_kernel<PREC, LS, SCALED, LAST, ContigIO<E>, R4, 2><<<(unsigned)(batch * (S >> KS::LOG2G)), KS::TPB,
+                                                                     KS::SMEM, stream>>>(
+          ContigIO<E>{static_cast<const E *>(in), static_cast<E *>(out), 1LL << log2n}, batch, log2n, P0, twp, r2e,
+          sgn);
+      return cudaGetLastError();
+    }
+  }
   if (items) {
     sweep_fft_kernel<PREC, LS, SCALED, LAST, GatherIO<E>, R4><<<(unsigned)blocks, K::TPB, K::SMEM, stream>>>(
         GatherIO<E>{items}, batch, log2n, P0, twp, r2e, sgn);
@@ -375,6 +396,13 @@ cudaError_t prepare_sweep_one() {
   using E = typename K::E;
   cudaError_t e = prepare_sweep_kernel(sweep_fft_kernel<PREC, LS, SCALED, LAST, ContigIO<E>, R4>, K::SMEM, K::TPB);
   if (e != cudaSuccess) return e;
+  if constexpr (!R4) {
+    using KS = Sweep<PREC, LS, SCALED, LAST, R4, 2>;
+    if constexpr (KS::LOG2G < K::LOG2G) {
+      e = prepare_sweep_kernel(sweep_fft_kernel<PREC, LS, SCALED, LAST, ContigIO<E>, R4, 2>, KS::SMEM, KS::TPB);
+      if (e != cudaSuccess) return e;
+    }
+  }
   return prepare_sweep_kernel(sweep_fft_kernel<PREC, LS, SCALED, LAST, GatherIO<E>, R4>, K::SMEM, K::TPB);
 }
 
