@@ -40,8 +40,9 @@ __host__ __device__ constexpr int fused_log2r(int prec, int log2n, bool narrow =
   return log2n < r ? log2n : r;
 }
 
-// BT = 0: a block of T threads (one transform) when T >= 128, else of 256
-// threads (several transforms) per launch; BT > 0: the block size
+// BT = 0: a block of T threads (one transform) when T >= 64 (FP16/BF16) or
+// 128 (FP32), else of 256 threads (several transforms) per launch; BT > 0:
+// the block size
 // of the persistent batch kernel (T <= BT).
 template <int PREC, int LOG2N, int LOG2R, bool SCALED, int BT = 0>
 struct Fused {
@@ -49,11 +50,13 @@ struct Fused {
   static constexpr int N = 1 << LOG2N;
   static constexpr int R = 1 << LOG2R;
   static constexpr int T = N / R;                        // threads per transform
-  // one transform per block from T = 128 threads up (FP16/BF16 2^12: 69.4 ->
-  // 71.2 % of HBM against two per 256-thread block; FP32 2^11 96.6 -> 99.7 %);
-  // smaller transforms share 256-thread blocks (FP16 2^11 in 128-thread
-  // blocks: 73.8 -> 67.7 %)
-  static constexpr int BTH = BT > 0 ? BT : (T >= 128 ? T : 256);
+  // one transform per block from T = 64 threads up for FP16/BF16 and from
+  // T = 128 for FP32 (measured on B300 against 256-thread blocks of several
+  // transforms: FP16 2^12 69.4 -> 71.2 %, 2^11 73.8 -> 75.8 % of HBM, FP32
+  // 2^11 96.6 -> 99.7 %; FP32 2^10 in 64-thread blocks 102.6 -> 101.8 %,
+  // FP16 2^10 in 32-thread blocks 84.3 -> 80.7 %); smaller transforms share
+  // 256-thread blocks
+  static constexpr int BTH = BT > 0 ? BT : (T >= (PREC == kFP32 ? 128 : 64) ? T : 256);
   static constexpr int TPC = BTH / T;                    // transforms per block (tile)
   static constexpr int TPB = T * TPC;
   static constexpr int NSTAGES = (LOG2N + LOG2R - 1) / LOG2R;
