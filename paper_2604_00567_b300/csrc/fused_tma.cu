@@ -200,11 +200,16 @@ static cudaError_t prepare_tma_one(int *blocks_per_sm) {
   using M = FusedTma<PREC, LOG2N, LOG2R, false>;
   for (auto kern : {fused_tma_fft_kernel<PREC, LOG2N, LOG2R, false>, fused_tma_fft_kernel<PREC, LOG2N, LOG2R, true>}) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, M::SMEM);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
   }
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fused_tma_fft_kernel<PREC, LOG2N, LOG2R, true>,
-                                                       M::TPB, M::SMEM);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      blocks_per_sm, fused_tma_fft_kernel<PREC, LOG2N, LOG2R, true>, M::TPB, M::SMEM);
+  if (e != cudaSuccess) return e;
+  // carveout: the shared memory of the resident blocks, the rest stays L1
+  const int carve = carveout_for(M::SMEM, *blocks_per_sm);
+  for (auto kern : {fused_tma_fft_kernel<PREC, LOG2N, LOG2R, false>, fused_tma_fft_kernel<PREC, LOG2N, LOG2R, true>})
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, carve)) != cudaSuccess) return e;
+  return cudaSuccess;
 }
 
 template <int PREC, int LOG2N>
