@@ -511,7 +511,7 @@ def serve_trace(seconds: float, rate: float, seed: int = 2):
 
 
 def serve_measure(seconds: float = 1.0, rate: float = 20000.0, budget: int = 40_000_000_000,
-                  max_tick_bytes: int = 1 << 28, brief: bool = False, in_flight: int = 8):
+                  max_tick_bytes: int = 1 << 26, brief: bool = False, in_flight: int = 8):
     """Serving loop under the arrival trace: inputs resident on the device
     (read from per-precision pools), outputs in the server's 40 GB arena
     (freed at completion).  Latency = completion seen by the scheduler -
