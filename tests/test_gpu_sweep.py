@@ -102,3 +102,23 @@ def test_batch_of_eight_large(dsfft):
     y = gpu_fft(plan, x)
     for b in (0, 7):
         assert_bitexact(y[b:b + 1], gpu_fft(plan, x[b:b + 1]), f"batch member {b}")
+
+
+@pytest.mark.parametrize("prec,log2n", [("fp16", 20), ("fp32", 18), ("fp16", 21), ("bf16", 19)])
+def test_narrow_group_launch_matches_batched(dsfft, prec, log2n):
+    """One transform alone launches few enough blocks that the sweeps take
+    their narrow-group instances (a quarter of the groups per block); the
+    same transform inside a batch of 16 takes the default ones.  Both run
+    the same butterflies: the bytes must be identical, in both directions."""
+    import torch
+    N = 1 << log2n
+    batch = signals.device_signal(16, N, prec, seed=log2n)
+    plan = dsfft.Plan(N, prec, "dual_select")
+    assert plan.info()["kernel"] == 1
+    word = torch.int32 if prec == "fp32" else torch.int16
+    for d in (-1, 1):
+        together = plan.exec(batch, direction=d)
+        alone = [plan.exec(batch[b:b + 1].clone(), direction=d) for b in (0, 7, 15)]
+        torch.cuda.synchronize()
+        for k, b in enumerate((0, 7, 15)):
+            assert torch.equal(alone[k].view(word), together[b:b + 1].view(word)), (prec, log2n, d, b)
