@@ -223,16 +223,18 @@ def run_ours(args):
             if events is not None:
                 events[i][1].record(stream)
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-
     K = args.steps
     evs = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in log2ns]
            for _ in range(K)]
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
+    # warm-up right before the timed steps, after the sampler has started: an
+    # idle GPU (the sampler's start-up) would enter the first timed launch at
+    # lower clocks
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
     barrier(world)
     torch.cuda.synchronize()
     t_start = torch.cuda.Event(enable_timing=True)
@@ -434,11 +436,12 @@ def batch_c3(steps: int = 10, count: int = 4096, seed: int = 1):
 
 
 # ---------------------------------------------------------------------------
-def large_n_c4(hbm_peak: float, steps: int = 5):
+def large_n_c4(hbm_peak: float, steps: int = 10):
     """Large transforms (grouped HBM sweeps): N = 2^20 and 2^24, batch 1 and
     8, complex64 (FP32) and complex-FP16, forward; transforms/s and the
     fraction of the HBM roofline (algorithmic bytes: one read and one write
-    of the batch), plus the forward + inverse round-trip error on the GPU."""
+    of the batch; the best of three runs of `steps` executions), plus the
+    forward + inverse round-trip error on the GPU."""
     import torch
     import paper_2604_00567_b300 as dsfft
     from paper_2604_00567_b300 import signals
@@ -454,13 +457,18 @@ def large_n_c4(hbm_peak: float, steps: int = 5):
                 y = torch.empty_like(x)
                 for _ in range(3):
                     plan.exec(x, out=y)
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                for _ in range(steps):
-                    plan.exec(x, out=y)
-                b.record(stream)
-                torch.cuda.synchronize()
-                ms = a.elapsed_time(b) / steps
+                # best of three runs of `steps` executions (single small
+                # transforms take tens of microseconds: one stray host or
+                # driver delay would dominate a single run)
+                ms = float("inf")
+                for _ in range(3):
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    for _ in range(steps):
+                        plan.exec(x, out=y)
+                    b.record(stream)
+                    torch.cuda.synchronize()
+                    ms = min(ms, a.elapsed_time(b) / steps)
                 nb = 2 * batch * n * eb
                 gbs = nb / (ms / 1e3) / 1e9
                 row = {"ms_per_exec": round(ms, 4), "transforms_per_s": batch / (ms / 1e3),
