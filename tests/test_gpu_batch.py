@@ -106,6 +106,17 @@ def test_sweep_sizes_in_batch(dsfft):
     _check(items, outs, refs, emus)
 
 
+def test_sweep_sizes_in_graph(dsfft):
+    """Two-sweep groups (sweep 2 a programmatic dependent launch of sweep 1)
+    inside the captured graph, replayed twice."""
+    spec = [(18, "fp16", "dual_select", -1, 2, False), (19, "fp32", "dual_select", 1, 1, False),
+            (12, "bf16", "dual_select", -1, 3, False)]
+    batch, items, outs, refs, emus = _run(dsfft, spec, 15, graph=True, repeat=2)
+    info = batch.info()
+    assert info["large_groups"] == 2 and info["graph_ready"] == 1
+    _check(items, outs, refs, emus, "graph ")
+
+
 def test_batch_argument_errors(dsfft):
     import torch
     x = torch.zeros((1, 1000), dtype=torch.complex64, device="cuda")
