@@ -404,7 +404,12 @@ typedef struct fft_server_opts {
                                      request of a tick is always taken); 0 =
                                      no limit (default).  Smaller ticks finish
                                      sooner, which shortens the wait of the
-                                     requests that arrive while they run. */
+                                     requests that arrive while they run.
+                                     When set, a tick takes the admitted
+                                     backlog's share per tick slot, between
+                                     an eighth of this limit and the limit:
+                                     small ticks while the queue is short,
+                                     full ones under a backlog. */
     int32_t reserved[2];          /* must be zero */
 } fft_server_opts;
 

@@ -148,6 +148,7 @@ struct fft_server {
   std::unordered_map<uint64_t, Request *> by_ticket;
   std::deque<Request *> queued;     // FIFO awaiting admission
   std::deque<Request *> admitted;   // awaiting launch
+  int64_t admitted_bytes = 0;       // output bytes of `admitted`
   std::deque<uint64_t> done_order;  // tickets done, in completion order (poll's queue)
   uint64_t next_ticket = 1;
   int64_t submitted = 0, n_admitted = 0, completed = 0, released = 0, ticks = 0, transforms = 0;
@@ -207,6 +208,7 @@ void admit(fft_server *s) {
     r->state = kAdmitted;
     s->queued.pop_front();
     s->admitted.push_back(r);
+    s->admitted_bytes += r->bytes;
     ++s->n_admitted;
   }
 }
@@ -307,13 +309,23 @@ void scheduler(fft_server *s) {
       Slot &sl = s->slots[free_slot];
       sl.reqs.clear();
       int64_t small_count = 0, tick_bytes = 0;
+      // tick size: the admitted backlog spread over the tick slots, between
+      // an eighth of max_tick_bytes and max_tick_bytes (when that limit is
+      // set): a short queue gives small ticks that finish soon, a backlog
+      // full-size ticks that amortise each tick's launches
+      int64_t cap = s->opts.max_tick_bytes;
+      if (cap > 0) {
+        const int64_t share = s->admitted_bytes / (int64_t)s->slots.size();
+        cap = std::min(cap, std::max(cap / 8, share));
+      }
       while (!s->admitted.empty()) {
         Request *r = s->admitted.front();
         if (small_request(r) && small_count + r->req.count > s->opts.max_tick_transforms) break;
-        if (s->opts.max_tick_bytes > 0 && !sl.reqs.empty() && tick_bytes + r->bytes > s->opts.max_tick_bytes) break;
+        if (cap > 0 && !sl.reqs.empty() && tick_bytes + r->bytes > cap) break;
         tick_bytes += r->bytes;
         if (small_request(r)) small_count += r->req.count;
         s->admitted.pop_front();
+        s->admitted_bytes -= r->bytes;
         r->state = kLaunched;
         sl.reqs.push_back(r);
       }
