@@ -35,7 +35,7 @@ __device__ __forceinline__ void sw_stcs(uint32_t *p, uint32_t v) { __stcs(reinte
 // radix-4 passes with 16 points per thread; an odd LS (sweep 1 of an odd
 // log2 N) starts with the radix-2 pass of span 1.
 // GSHIFT: a block of 2^GSHIFT times fewer groups (at least 4) than the
-// default, for launches with fewer blocks than the GPU has SMs (one or a few
+// default, for launches of at most one block per two SMs (one or a few
 // transforms): shorter runs per warp, more blocks.
 template <int PREC, int LS, bool SCALED, bool LAST, bool R4 = false, int GSHIFT = 0>
 struct Sweep {
