@@ -302,9 +302,10 @@ static cudaError_t launch_cluster_one(const void *in, void *out, const BatchItem
 }
 
 // Carveout: the shared memory of the CTAs the register budget lets reside
-// (MINB); the rest of the SM's L1/shared array stays L1 for the phase-2
-// twiddles (measured on B300, FP16 N = 2^16: 41.1 % of HBM against 37.7 %
-// with the maximum carveout; one CTA fewer per SM for a larger L1: 34.3 %).
+// (MINB); the rest of the SM's L1/shared array stays L1 (measured on B300,
+// FP16 N = 2^16: 41.1 % of HBM against 37.7 % with the maximum carveout,
+// with fewer MIO-throttle and barrier stalls; one CTA fewer per SM for a
+// larger L1: 34.3 %).
 template <class F>
 static cudaError_t prepare_cluster_kernel(F kern, int smem, int nblk) {
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

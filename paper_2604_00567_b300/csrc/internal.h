@@ -18,7 +18,9 @@ enum Prec : int { kFP32 = 0, kFP16 = 1, kBF16 = 2 };
 // configuration of the SM (0, 8, 16, 32, 64, 100, 132, 164, 196 or 228 KB on
 // this architecture) at or above the percentage, so the percentage is that of
 // the smallest configuration that fits, rounded down.  What the blocks do not
-// need stays L1, where the per-lane twiddle loads of the large-N kernels hit.
+// need stays L1 (measured faster than the maximum carveout for the cluster,
+// sweep and batch kernels: the cluster kernel's MIO-throttle and barrier
+// stalls drop while its L1 hit rate hardly changes).
 inline int carveout_for(int smem, int blocks) {
   static const int kConfigKB[] = {0, 8, 16, 32, 64, 100, 132, 164, 196, 228};
   const long long need = (long long)(smem + 1024) * (blocks > 0 ? blocks : 1);
@@ -131,7 +133,7 @@ cudaError_t launch_fused_tma(int prec, int log2n, bool scaled, const void *in, v
 void sweep_split(int log2n, int *ls1, int *ls2);
 bool sweep_ls1_valid(int log2n, int ls1);
 // SMs of the current device (cached per device; 0 when unknown): the sweeps
-// switch to their narrow-group kernels below one block per SM.
+// switch to their narrow-group kernels at or below one block per two SMs.
 int sweep_sm_count();
 cudaError_t prepare_sweeps(int prec, int log2n, int ls1 = 0);
 // `items` (device array, one per transform) replaces in/out when non-null.
